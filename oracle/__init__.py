@@ -1,0 +1,106 @@
+"""CPU oracle for exact polyhedral geodesic distance - TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
+import this package.  It wraps ``ich_oracle.cpp`` (sequential FP64 Chen-Han/Xin-Wang,
+Algorithm 2 of the paper) and ``mlp_oracle.py`` (FP64 reference of the selection
+controller's network).  It shares no code with the CUDA path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+ORDER_PQ, ORDER_FIFO, ORDER_RANDOM = 0, 1, 2
+NO_CH, NO_ICH = 4, 8
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library in-tree (plain g++, portable flags)."""
+    src = os.path.join(_HERE, "ich_oracle.cpp")
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-shared", "-fPIC", "-o", _SO, src])
+    return _SO
+
+
+def load_library(path: str):
+    """Load an oracle build from ``path`` (the tests also load mutated copies)."""
+    lib = ctypes.CDLL(path)
+    _declare(lib)
+    return lib
+
+
+def _declare(lib):
+    lib.oracle_geodesic.restype = ctypes.c_int
+    lib.oracle_geodesic.argtypes = [
+        ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+        ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+        ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.oracle_vertex_angles.restype = ctypes.c_int
+    lib.oracle_vertex_angles.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                         ctypes.c_void_p, ctypes.c_void_p]
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build()
+        lib = ctypes.CDLL(_SO)
+        _declare(lib)
+        _lib = lib
+    return _lib
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def geodesic(vertices, faces, source=None, *, face=None, bary=None, sources=None, flags: int = 0,
+             targets=None, max_windows: int = 0, lib=None):
+    """Exact geodesic distance to every vertex.  Returns (dist[V], stats dict).
+
+    source: vertex id; or face/bary for a point inside a face; or sources (list) for the
+    multi-source field (distance to the nearest source)."""
+    lib = lib or _load()
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    f = np.ascontiguousarray(faces, dtype=np.int32)
+    out = np.empty(v.shape[0], dtype=np.float64)
+    stats = np.zeros(4, dtype=np.int64)
+    b = np.zeros(3, dtype=np.float64)
+    srcs = np.zeros(1, dtype=np.int32)
+    if sources is not None:
+        kind, sv, sf = 2, 0, 0
+        srcs = np.ascontiguousarray(sources, dtype=np.int32)
+    elif face is not None:
+        kind, sv, sf = 1, 0, int(face)
+        b = np.ascontiguousarray(bary, dtype=np.float64)
+    else:
+        kind, sv, sf = 0, int(source), 0
+    t = np.zeros(1, dtype=np.int32) if targets is None else np.ascontiguousarray(targets, dtype=np.int32)
+    nt = 0 if targets is None else int(t.shape[0])
+    rc = lib.oracle_geodesic(v.shape[0], v.ctypes.data, f.shape[0], f.ctypes.data, kind, sv, sf,
+                             b.ctypes.data, int(srcs.shape[0]), srcs.ctypes.data, int(flags),
+                             int(max_windows), nt, t.ctypes.data, out.ctypes.data, stats.ctypes.data)
+    if rc != 0:
+        raise OracleError(f"oracle_geodesic failed with code {rc}")
+    return out, {"created": int(stats[0]), "propagated": int(stats[1]), "peak": int(stats[2]),
+                 "events": int(stats[3])}
+
+
+def vertex_angles(vertices, faces):
+    lib = _load()
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    f = np.ascontiguousarray(faces, dtype=np.int32)
+    th = np.empty(v.shape[0])
+    ps = np.empty(v.shape[0], dtype=np.uint8)
+    rc = lib.oracle_vertex_angles(v.shape[0], v.ctypes.data, f.shape[0], f.ctypes.data, th.ctypes.data,
+                                  ps.ctypes.data)
+    if rc != 0:
+        raise OracleError(f"oracle_vertex_angles failed with code {rc}")
+    return th, ps.astype(bool)
