@@ -1,0 +1,174 @@
+/*
+ * pch.h - C ABI of the GB300 (sm_103a) Parallel Chen-Han exact-geodesic library.
+ *
+ * Computes exact single-source-all-destination geodesic distance on a triangle mesh
+ * with the iterated four-phase loop of Ying, Xin and He, "Parallel Chen-Han (PCH)
+ * Algorithm for Discrete Geodesics": window selection, window propagation, data
+ * organisation and events processing (Section 4.2, Algorithm 1), every phase a CUDA
+ * kernel.  Plain C types only: pointers, sizes and status codes.
+ *
+ * Conventions for every entry point:
+ *  - Host pointers unless an argument says "device".  The library copies what it keeps;
+ *    the caller may free its inputs as soon as a call returns.
+ *  - Results are written only on success (PCH_OK).  On error nothing the caller owns is
+ *    modified, the status is returned and pch_last_error() describes it.
+ *  - No exceptions cross the ABI.  Calls are synchronous with respect to the host
+ *    unless pch_options.out_on_device is set, in which case results are complete when
+ *    pch_options.stream (or the legacy default stream) reaches the end of the call.
+ *  - Calls that share a pch_mesh (it carries the solver workspace) must not run
+ *    concurrently from several host threads.
+ */
+#ifndef PCH_H_
+#define PCH_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque mesh handle: the half-edge structure of Section 4.1 plus per-half-edge
+ * unfolding frames, resident in device memory, and the solver workspace.  Owned by
+ * the library; release it with pch_destroy(). */
+typedef struct pch_mesh pch_mesh;
+
+typedef enum {
+    PCH_OK = 0,
+    PCH_ERR_INVALID_ARG = 1,   /* null pointer, index out of range, non-finite coordinate */
+    PCH_ERR_NONMANIFOLD = 2,   /* an oriented edge used twice, or a vertex whose faces do not form one fan */
+    PCH_ERR_DEGENERATE = 3,    /* a face with (near) zero area or a repeated vertex */
+    PCH_ERR_OOM = 4,           /* device memory allocation failed */
+    PCH_ERR_CUDA = 5,          /* a CUDA runtime call failed (message in pch_last_error) */
+    PCH_ERR_CAPACITY = 6,      /* a size limit was exceeded (see the entry point) */
+    PCH_ERR_TIMEOUT = 7        /* the iteration cap (pch_options.max_iters) was reached */
+} pch_status;
+
+/* A source: a mesh vertex (kind 0), or a point inside face `face` with barycentric
+ * weights `bary` over that face's three corners in their stored order (kind 1).
+ * Algorithm 1 takes sources in V; the face point is the same initialisation applied
+ * to the three edges of the face. */
+typedef struct {
+    int32_t kind;
+    int32_t vertex;
+    int32_t face;
+    int32_t reserved;
+    double bary[3];
+} pch_source;
+
+/* Selection control (Step 1 of Section 4.2). */
+enum {
+    PCH_CONTROL_PLAIN = 0,    /* fixed window count k per iteration (the paper's k) */
+    PCH_CONTROL_LEARNED = 1,  /* MLP controller maps frontier statistics to the threshold;
+                                 falls back to PLAIN on a non-finite or out-of-range output */
+    PCH_CONTROL_STRIDED = 2   /* the paper's approximate k-selection of Section 5.1 */
+};
+
+/* Iteration driver. */
+enum {
+    PCH_LOOP_GRAPH = 0,       /* iterations replayed from a CUDA graph with a device-side
+                                 termination condition (default) */
+    PCH_LOOP_HOST = 1         /* host launches every iteration and reads the pending count */
+};
+
+/* Solve options.  Pass NULL for the defaults; a zero field also means "default". */
+typedef struct {
+    int32_t control;          /* PCH_CONTROL_* */
+    int32_t loop;             /* PCH_LOOP_* */
+    int64_t k;                /* PLAIN/STRIDED: windows selected per instance per iteration */
+    int64_t max_iters;        /* iteration cap; exceeded -> PCH_ERR_TIMEOUT (default 2^31) */
+    void* stream;             /* cudaStream_t to run on (NULL = legacy default stream) */
+    int32_t out_on_device;    /* nonzero: output pointers are device pointers */
+    int32_t block;            /* threads per block of the propagation kernel (0 = tuned) */
+    int32_t flags;            /* PCH_FLAG_* */
+    int32_t reserved;
+} pch_options;
+
+enum {
+    PCH_FLAG_NO_TRIM = 1,     /* skip the per-edge trimming of Step 4 */
+    PCH_FLAG_FULL_FAN = 2,    /* pseudo-source fans over the whole one-ring instead of the
+                                 fanned area of Fig. `fig:propagation`(c) */
+    PCH_FLAG_TRACE = 4        /* record per-iteration controller features (pch_trace_fetch) */
+};
+
+/* Per-call statistics (the columns of Table `tab:speedup`: time, windows, peak windows). */
+typedef struct {
+    int64_t iterations;
+    int64_t windows_created;      /* windows written to the pool (children + fans) */
+    int64_t windows_propagated;   /* selected windows that passed the filter and were propagated */
+    int64_t peak_pending;         /* largest pending pool seen */
+    double ms_total;              /* device time of the solve loop (CUDA events) */
+    double ms_setup;              /* device time of initialisation */
+    int64_t bytes_workspace;      /* device bytes held by the solver workspace */
+} pch_stats;
+
+/* Build a mesh: host arrays `vertices` (n_vertices x 3 doubles, xyz) and `faces`
+ * (n_faces x 3 int32 vertex ids, one consistent orientation).  The half-edge table,
+ * edge lengths, per-half-edge unfolding frames, vertex total angles and the
+ * saddle/boundary classification of Section 3 are computed on the device (Section 4.1:
+ * the method needs only the metric).  Errors: INVALID_ARG, NONMANIFOLD, DEGENERATE,
+ * OOM, CUDA.  On success *out owns the device data. */
+pch_status pch_create_mesh(const double* vertices, int32_t n_vertices, const int32_t* faces,
+                           int32_t n_faces, pch_mesh** out);
+
+/* Counts of a mesh: vertices, faces, boundary half-edges, pseudo-source vertices. */
+pch_status pch_mesh_info(const pch_mesh* m, int32_t* n_vertices, int32_t* n_faces,
+                         int32_t* n_boundary_half_edges, int32_t* n_pseudo_vertices);
+
+/* Single-source-all-destination exact geodesic distance (Algorithm 1).  out_dist:
+ * n_vertices doubles (host, or device if opt->out_on_device), caller-owned.  The
+ * source vertex gets exactly 0; vertices unreachable from the source get +inf.
+ * stats may be NULL.  Errors: INVALID_ARG, OOM, CUDA, CAPACITY, TIMEOUT. */
+pch_status pch_solve(pch_mesh* m, const pch_source* src, const pch_options* opt, double* out_dist,
+                     pch_stats* stats);
+
+/* Multiple-source-all-destination field (Section 4.2, source set S; Table
+ * `tab:multiple`): distance to the nearest of the n_sources sources. */
+pch_status pch_solve_multi(pch_mesh* m, const pch_source* srcs, int32_t n_sources,
+                           const pch_options* opt, double* out_dist, pch_stats* stats);
+
+/* Many independent solves in one launch sequence: instance i solves meshes[i] from
+ * srcs[i] into out_dists[i] (n_vertices of meshes[i] doubles each).  Instances may
+ * share a mesh (many sources on one mesh) or use different meshes of any size.  All
+ * meshes must live on the current device.  The workspace is held by meshes[0]. */
+pch_status pch_solve_batch(pch_mesh* const* meshes, const pch_source* srcs, int32_t n_instances,
+                           const pch_options* opt, double* const* out_dists, pch_stats* stats);
+
+/* Release a mesh and its workspace (NULL is a no-op). */
+void pch_destroy(pch_mesh* m);
+
+/* Message of the last error on the calling host thread ("" if none). */
+const char* pch_last_error(void);
+
+/* ---- learned selection controller (build-only; no counterpart in the paper) -----------
+ * A 3 x 64 hidden-layer fp32 MLP maps per-iteration frontier statistics to the next
+ * selection threshold.  Weights are a flat fp32 array of pch_mlp_num_params() values
+ * (layer by layer: W then b, W row-major [out][in]). */
+int32_t pch_mlp_num_features(void);
+int32_t pch_mlp_num_params(void);
+/* Install weights used by PCH_CONTROL_LEARNED (host array, copied). */
+pch_status pch_mlp_set_weights(const float* params, int32_t n_params);
+/* Forward pass on the device: x (n x num_features), y (n) device pointers. */
+pch_status pch_mlp_forward(const float* params_dev, const float* x_dev, int32_t n, float* y_dev,
+                           void* stream);
+/* Gradient of 0.5 * mean((y - target)^2) w.r.t. the parameters (device pointers);
+ * grad_dev gets num_params floats, loss_dev one float.  Deterministic reduction. */
+pch_status pch_mlp_backward(const float* params_dev, const float* x_dev, const float* target_dev,
+                            int32_t n, float* grad_dev, float* loss_dev, void* stream);
+/* One Adam step in place (device pointers; m_dev, v_dev: moment buffers; t >= 1). */
+pch_status pch_mlp_adam(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev,
+                        int32_t t, float lr, void* stream);
+/* Per-iteration features and chosen thresholds of the last solve on this mesh's
+ * workspace (the controller's training traces): up to max_rows rows of
+ * num_features floats into features (host), selected fraction into chosen (host). */
+pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float* chosen,
+                           int32_t* n_rows);
+
+/* ---- measurement helpers ---------------------------------------------------------- */
+/* Sustained FP64 FMA rate of this GPU (TFLOP/s, 2 flops per FMA) from a
+ * register-resident DFMA loop; the roofline denominator for the propagation kernel. */
+pch_status pch_measure_fp64_peak(double* tflops);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PCH_H_ */

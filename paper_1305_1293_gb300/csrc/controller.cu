@@ -1,0 +1,258 @@
+// Learned selection controller: parameters, training kernels (forward, backward, Adam)
+// and the FP64 peak microbenchmark.  The network and its role are described in
+// controller.cuh; none of this has a counterpart in the paper, which fixes k by hand
+// (Section 5.2).
+#include <cmath>
+#include <cstdlib>
+#include <vector>
+
+#include "pch_host.h"
+#include "solver.cuh"
+
+namespace pch {
+
+static float* g_mlp_dev = nullptr;   // installed weights (device), used by PCH_CONTROL_LEARNED
+static int g_mlp_dev_id = -1;
+
+const float* mlp_device_params() { return g_mlp_dev; }
+
+long long default_k() {
+    const char* e = std::getenv("PCH_DEFAULT_K");
+    if (e) {
+        long long v = std::atoll(e);
+        if (v > 0) return v;
+    }
+    return 32768;
+}
+
+// ---------------------------------------------------------------- training kernels
+// One block of kHidden threads per sample.  act: [n][3][kHidden] post-ReLU activations.
+__global__ void __launch_bounds__(kHidden) k_mlp_fwd(const float* __restrict__ p, const float* __restrict__ x, int n,
+                                                     float* __restrict__ y, float* __restrict__ act) {
+    __shared__ float xs[kFeatures], h0[kHidden], h1[kHidden], h2[kHidden];
+    const int t = threadIdx.x;
+    for (int b = blockIdx.x; b < n; b += gridDim.x) {
+        if (t < kFeatures) xs[t] = x[(size_t)b * kFeatures + t];
+        __syncthreads();
+        float s = p[kMlpB1 + t];
+        for (int i = 0; i < kFeatures; ++i) s = fmaf(p[kMlpW1 + t * kFeatures + i], xs[i], s);
+        h0[t] = fmaxf(s, 0.f);
+        __syncthreads();
+        s = p[kMlpB2 + t];
+        for (int i = 0; i < kHidden; ++i) s = fmaf(p[kMlpW2 + t * kHidden + i], h0[i], s);
+        h1[t] = fmaxf(s, 0.f);
+        __syncthreads();
+        s = p[kMlpB3 + t];
+        for (int i = 0; i < kHidden; ++i) s = fmaf(p[kMlpW3 + t * kHidden + i], h1[i], s);
+        h2[t] = fmaxf(s, 0.f);
+        __syncthreads();
+        if (act) {
+            act[((size_t)b * 3 + 0) * kHidden + t] = h0[t];
+            act[((size_t)b * 3 + 1) * kHidden + t] = h1[t];
+            act[((size_t)b * 3 + 2) * kHidden + t] = h2[t];
+        }
+        if (t == 0) {
+            float o = p[kMlpB4];
+            for (int i = 0; i < kHidden; ++i) o = fmaf(p[kMlpW4 + i], h2[i], o);
+            y[b] = o;
+        }
+        __syncthreads();
+    }
+}
+
+// Per-sample back-propagation of L = 0.5 mean((y - target)^2): dlt [n][3][kHidden]
+// holds dL/dz for each hidden layer's pre-activation; dy[n] = (y - t) / n.
+__global__ void __launch_bounds__(kHidden) k_mlp_bwd(const float* __restrict__ p, const float* __restrict__ act,
+                                                     const float* __restrict__ y, const float* __restrict__ target,
+                                                     int n, float* __restrict__ dlt, float* __restrict__ dy) {
+    __shared__ float d2[kHidden], d1[kHidden];
+    const int t = threadIdx.x;
+    for (int b = blockIdx.x; b < n; b += gridDim.x) {
+        const float* a = act + (size_t)b * 3 * kHidden;
+        const float e = (y[b] - target[b]) / (float)n;
+        if (t == 0) dy[b] = e;
+        float v = a[2 * kHidden + t] > 0.f ? e * p[kMlpW4 + t] : 0.f;
+        d2[t] = v;
+        dlt[((size_t)b * 3 + 2) * kHidden + t] = v;
+        __syncthreads();
+        float s = 0.f;
+        for (int j = 0; j < kHidden; ++j) s = fmaf(p[kMlpW3 + j * kHidden + t], d2[j], s);
+        v = a[kHidden + t] > 0.f ? s : 0.f;
+        d1[t] = v;
+        dlt[((size_t)b * 3 + 1) * kHidden + t] = v;
+        __syncthreads();
+        s = 0.f;
+        for (int j = 0; j < kHidden; ++j) s = fmaf(p[kMlpW2 + j * kHidden + t], d1[j], s);
+        dlt[((size_t)b * 3 + 0) * kHidden + t] = a[t] > 0.f ? s : 0.f;
+        __syncthreads();
+    }
+}
+
+// One thread per parameter, sums over the samples in order: deterministic.
+__global__ void k_mlp_grad(const float* __restrict__ x, const float* __restrict__ act, const float* __restrict__ dlt,
+                           const float* __restrict__ dy, int n, float* __restrict__ grad) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < kMlpParams; q += gridDim.x * blockDim.x) {
+        float s = 0.f;
+        if (q < kMlpB1) {
+            int o = (q - kMlpW1) / kFeatures, i = (q - kMlpW1) % kFeatures;
+            for (int b = 0; b < n; ++b) s = fmaf(dlt[((size_t)b * 3 + 0) * kHidden + o], x[(size_t)b * kFeatures + i], s);
+        } else if (q < kMlpW2) {
+            int o = q - kMlpB1;
+            for (int b = 0; b < n; ++b) s += dlt[((size_t)b * 3 + 0) * kHidden + o];
+        } else if (q < kMlpB2) {
+            int o = (q - kMlpW2) / kHidden, i = (q - kMlpW2) % kHidden;
+            for (int b = 0; b < n; ++b)
+                s = fmaf(dlt[((size_t)b * 3 + 1) * kHidden + o], act[((size_t)b * 3 + 0) * kHidden + i], s);
+        } else if (q < kMlpW3) {
+            int o = q - kMlpB2;
+            for (int b = 0; b < n; ++b) s += dlt[((size_t)b * 3 + 1) * kHidden + o];
+        } else if (q < kMlpB3) {
+            int o = (q - kMlpW3) / kHidden, i = (q - kMlpW3) % kHidden;
+            for (int b = 0; b < n; ++b)
+                s = fmaf(dlt[((size_t)b * 3 + 2) * kHidden + o], act[((size_t)b * 3 + 1) * kHidden + i], s);
+        } else if (q < kMlpW4) {
+            int o = q - kMlpB3;
+            for (int b = 0; b < n; ++b) s += dlt[((size_t)b * 3 + 2) * kHidden + o];
+        } else if (q < kMlpB4) {
+            int i = q - kMlpW4;
+            for (int b = 0; b < n; ++b) s = fmaf(dy[b], act[((size_t)b * 3 + 2) * kHidden + i], s);
+        } else {
+            for (int b = 0; b < n; ++b) s += dy[b];
+        }
+        grad[q] = s;
+    }
+}
+
+__global__ void k_mlp_loss(const float* __restrict__ y, const float* __restrict__ target, int n, float* loss) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < n; b += blockDim.x) {
+        double e = (double)y[b] - (double)target[b];
+        s += e * e;
+    }
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = (float)(0.5 * sh[0] / n);
+}
+
+__global__ void k_mlp_adam(float* p, const float* __restrict__ g, float* m, float* v, int t, float lr) {
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - powf(b1, (float)t), c2 = 1.f - powf(b2, (float)t);
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < kMlpParams; q += gridDim.x * blockDim.x) {
+        float gq = g[q];
+        float mq = b1 * m[q] + (1.f - b1) * gq;
+        float vq = b2 * v[q] + (1.f - b2) * gq * gq;
+        m[q] = mq;
+        v[q] = vq;
+        p[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + eps);
+    }
+}
+
+// ---------------------------------------------------------------- FP64 peak
+__global__ void k_dfma_peak(double* out, int iters) {
+    double a0 = threadIdx.x * 1e-9, a1 = a0 + 1e-3, a2 = a0 + 2e-3, a3 = a0 + 3e-3;
+    double a4 = a0 + 4e-3, a5 = a0 + 5e-3, a6 = a0 + 6e-3, a7 = a0 + 7e-3;
+    const double m = 0.999999, c = 1e-7;
+    for (int i = 0; i < iters; ++i) {
+        a0 = fma(a0, m, c); a1 = fma(a1, m, c); a2 = fma(a2, m, c); a3 = fma(a3, m, c);
+        a4 = fma(a4, m, c); a5 = fma(a5, m, c); a6 = fma(a6, m, c); a7 = fma(a7, m, c);
+    }
+    double s = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
+    if (s == 12345.678) out[0] = s;   // keep the chains alive
+}
+
+}  // namespace pch
+
+using namespace pch;
+
+extern "C" int32_t pch_mlp_num_features(void) { return kFeatures; }
+extern "C" int32_t pch_mlp_num_params(void) { return kMlpParams; }
+
+extern "C" pch_status pch_mlp_set_weights(const float* params, int32_t n_params) {
+    clear_error();
+    if (!params || n_params != kMlpParams) return set_error(PCH_ERR_INVALID_ARG, "expected %d parameters", kMlpParams);
+    for (int i = 0; i < n_params; ++i)
+        if (!std::isfinite(params[i])) return set_error(PCH_ERR_INVALID_ARG, "non-finite weight %d", i);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (g_mlp_dev && g_mlp_dev_id != dev) g_mlp_dev = nullptr;   // other device: reallocate
+    if (!g_mlp_dev) {
+        PCH_CUDA(cudaMalloc(&g_mlp_dev, sizeof(float) * kMlpParams));
+        g_mlp_dev_id = dev;
+    }
+    PCH_CUDA(cudaMemcpy(g_mlp_dev, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice));
+    return PCH_OK;
+}
+
+extern "C" pch_status pch_mlp_forward(const float* params_dev, const float* x_dev, int32_t n, float* y_dev,
+                                      void* stream) {
+    clear_error();
+    if (!params_dev || !x_dev || !y_dev || n <= 0) return set_error(PCH_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    k_mlp_fwd<<<std::min(n, 65535), kHidden, 0, s>>>(params_dev, x_dev, n, y_dev, nullptr);
+    PCH_CUDA(cudaGetLastError());
+    return PCH_OK;
+}
+
+extern "C" pch_status pch_mlp_backward(const float* params_dev, const float* x_dev, const float* target_dev, int32_t n,
+                                       float* grad_dev, float* loss_dev, void* stream) {
+    clear_error();
+    if (!params_dev || !x_dev || !target_dev || !grad_dev || !loss_dev || n <= 0)
+        return set_error(PCH_ERR_INVALID_ARG, "bad arguments");
+    cudaStream_t s = (cudaStream_t)stream;
+    // scratch: activations, deltas, outputs
+    float* scratch = nullptr;
+    size_t nact = (size_t)n * 3 * kHidden;
+    PCH_CUDA(cudaMallocAsync(&scratch, sizeof(float) * (2 * nact + 2 * (size_t)n), s));
+    float* act = scratch;
+    float* dlt = act + nact;
+    float* y = dlt + nact;
+    float* dy = y + n;
+    int g = std::min(n, 65535);
+    k_mlp_fwd<<<g, kHidden, 0, s>>>(params_dev, x_dev, n, y, act);
+    k_mlp_bwd<<<g, kHidden, 0, s>>>(params_dev, act, y, target_dev, n, dlt, dy);
+    k_mlp_grad<<<(kMlpParams + 255) / 256, 256, 0, s>>>(x_dev, act, dlt, dy, n, grad_dev);
+    k_mlp_loss<<<1, 256, 0, s>>>(y, target_dev, n, loss_dev);
+    cudaError_t e = cudaGetLastError();
+    cudaFreeAsync(scratch, s);
+    PCH_CUDA(e);
+    return PCH_OK;
+}
+
+extern "C" pch_status pch_mlp_adam(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev, int32_t t,
+                                   float lr, void* stream) {
+    clear_error();
+    if (!params_dev || !grad_dev || !m_dev || !v_dev || t < 1) return set_error(PCH_ERR_INVALID_ARG, "bad arguments");
+    k_mlp_adam<<<(kMlpParams + 255) / 256, 256, 0, (cudaStream_t)stream>>>(params_dev, grad_dev, m_dev, v_dev, t, lr);
+    PCH_CUDA(cudaGetLastError());
+    return PCH_OK;
+}
+
+extern "C" pch_status pch_measure_fp64_peak(double* tflops) {
+    clear_error();
+    if (!tflops) return set_error(PCH_ERR_INVALID_ARG, "null output");
+    double* out = nullptr;
+    PCH_CUDA(cudaMalloc(&out, sizeof(double)));
+    const int blocks = sm_count() * 8, threads = 256, iters = 1 << 14;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    k_dfma_peak<<<blocks, threads>>>(out, 256);   // warm-up
+    cudaEventRecord(a);
+    k_dfma_peak<<<blocks, threads>>>(out, iters);
+    cudaEventRecord(b);
+    cudaError_t e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    cudaFree(out);
+    PCH_CUDA(e);
+    double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
+    *tflops = flops / (ms * 1e-3) / 1e12;
+    return PCH_OK;
+}

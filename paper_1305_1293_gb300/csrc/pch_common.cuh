@@ -1,0 +1,154 @@
+// Internal device data layout of the PCH library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pch.h"
+
+namespace pch {
+
+// ---- tolerances (same values, independently written, as the CPU oracle) -------------
+// "A = v0", "B = v1" and vertex occupancy are decided within kEpsSnap * |e|.
+constexpr double kEpsSnap = 1e-12;
+// Windows narrower than kEpsTiny * |e| are dropped (Section 5.3 drops tiny windows).
+constexpr double kEpsTiny = 1e-12;
+// A filter removes a window only when it is worse by more than this relative margin.
+constexpr double kDomRel = 1e-12;
+
+constexpr unsigned long long kEmptyAngle = ~0ull;
+constexpr int kAngleXBits = 24;                       // low bits of a packed angle_split word
+constexpr unsigned long long kAngleXMask = (1ull << kAngleXBits) - 1;
+constexpr unsigned kPseudoBit = 0x80000000u;          // vertex id flag: saddle or boundary vertex
+
+// Selection histogram: bin b covers (key - ref)/lbar in [(2^(b/16)-1)/4, (2^((b+1)/16)-1)/4).
+constexpr int kBins = 256;
+constexpr float kBinsPerOctave = 16.f;
+constexpr float kBinScale = 4.f;
+
+// Controller features (a8): see controller.cu.
+constexpr int kFeatures = 24;
+constexpr int kHidden = 64;
+
+// ---- mesh (Section 4.1): one 96-byte record per half-edge --------------------------
+// Frame of half-edge h = (v0 -> v1) in face f: v0 at the origin, v1 at (L, 0), the
+// opposite vertex v2 at (xc, yc), yc > 0.  A window on h propagates into f.
+struct __align__(16) HERec {
+    double L, xc, yc;      // edge length and apex position
+    double L1, L2;         // |v1 v2|, |v2 v0|
+    double iL1, iL2, iL;   // reciprocals
+    int tw1;               // twin of next(h) = (v2 -> v1) in the neighbour: right child's edge
+    int tw2;               // twin of prev(h) = (v0 -> v2) in the neighbour: left child's edge
+    unsigned v0, v1, v2;   // vertex ids | kPseudoBit
+    int twin;              // twin of h (-1 on the boundary)
+};
+static_assert(sizeof(HERec) == 96, "HERec layout");
+
+struct DevMesh {
+    int nv, nf, nh;
+    double lbar;           // mean edge length
+    HERec* rec;            // [nh]
+    int* vstart;           // [nv + 1] CSR of outgoing half-edges, one-ring order
+    int* vlist;            // [nh]
+    double* hang;          // [nh] corner angle at the start vertex of each half-edge
+    double* vtheta;        // [nv] total angle (Section 3)
+    double* vphi;          // [nh] angular position of each outgoing half-edge around its start vertex
+    unsigned char* vflag;  // [nv] bit0 boundary, bit1 pseudo-source capable
+};
+
+// ---- windows: structure of arrays (Section 3's 6-tuple, with the pseudo-source kept
+// as coordinates (px, py) in the edge frame instead of (d0, d1)) ------------------------
+struct WinSoA {
+    int* he;        // half-edge (local to the instance's mesh); -1 = empty slot
+    int* inst;      // instance
+    double* d;      // pseudo-source distance to the source
+    double* A;      // interval [A, B] along the edge from its start vertex
+    double* B;
+    double* px;     // pseudo-source position in the edge frame (py < 0)
+    double* py;
+    double* key;    // d + dist(I, [A, B]): the window's distance back to the source
+};
+
+// ---- instances -------------------------------------------------------------------
+struct Inst {
+    const HERec* rec;
+    const int* vstart;
+    const int* vlist;
+    const double* vphi;
+    const double* vtheta;
+    unsigned long long* g;      // geod_dist[] as ordered u64 images of nonnegative doubles
+    unsigned long long* ang;    // angle_split[]: packed (rounded-up distance, crossing position)
+    unsigned* stamp;            // per-vertex iteration stamp (one fan request per iteration)
+    double* fan_phi;            // per-vertex incoming direction of the best event this iteration
+    int nv, nh;
+    long long keybase;          // sort key = keybase + half-edge
+    double lbar;
+    double ilbar;
+};
+
+struct InstCtl {
+    double tau;                 // selection threshold of the current iteration
+    double ref;                 // histogram reference (a lower bound of every pending key)
+    unsigned long long kmin;    // running min of the keys written to the next pool (bits)
+    int n_pending;              // pending windows of this instance in the current pool
+    int n_next;                 // pending windows written to the next pool
+    int n_sel;                  // selected this iteration
+    int n_child;                // children written this iteration
+    long long k_target;         // plain control: windows to select
+    float last_ratio;           // children / selected of the previous iteration
+    float ctl_out;              // last controller output
+    int active;
+    int pad;
+};
+
+// ---- global counters of one solve -------------------------------------------------
+struct Counters {
+    int n_pending;          // windows in the current pool
+    int n_rest;             // not-selected windows copied to the next pool
+    int n_sel;              // selected windows (work list)
+    int n_child;            // slots used in the child arena
+    int n_req;              // fan requests for this iteration
+    int n_req_next;         // fan requests for the next iteration
+    int n_app;              // windows appended to the next pool
+    int iter;
+    int error;              // bitmask of kErr*
+    int done;
+    int sort_bits;          // bits of the sort key
+    int halt;               // set by k_finish when the loop must stop; every kernel no-ops
+    unsigned long long created, propagated, filtered, trimmed, peak_pending;
+};
+
+enum : int {
+    kErrPoolFull = 1,
+    kErrReqFull = 2,
+    kErrIter = 4,
+    kErrNaN = 8,
+};
+
+// Capacities and buffers of the solve workspace.
+struct Work {
+    WinSoA pool[2];         // current / next pending pool
+    WinSoA sel;             // selected windows
+    WinSoA arena;           // children of this iteration (unsorted)
+    int pool_cap, sel_cap, arena_cap, req_cap;
+    int2* req[2];           // fan requests (inst, vertex)
+    unsigned* sort_key[2];
+    int* sort_val[2];
+    int* sort_hist;         // radix histograms
+    int sort_blocks;
+    unsigned* hist[2];      // selection histograms [n_inst * kBins]
+    Inst* inst;
+    InstCtl* ctl;
+    int n_inst;
+    Counters* cnt;
+    float* trace;           // controller trace rows
+    int trace_cap;
+    int* trace_rows;
+};
+
+// Ordered u64 image of a nonnegative double (atomicMin-able, Section 4.2 Step 4).
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+__device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
+__device__ __forceinline__ bool dominated(double lhs, double rhs) { return lhs > rhs * (1.0 + kDomRel); }
+
+}  // namespace pch

@@ -1,0 +1,1132 @@
+// The four-phase PCH iteration (Section 4.2, Algorithm 1) on sm_103a.
+//
+// One iteration, every phase a kernel over device-resident counts (fixed grids, so the
+// whole iteration can be replayed from a CUDA graph):
+//   k_tau        Step 1a: per-instance selection threshold from the key histogram
+//                (plain: the k-th nearest window, the paper's k; learned: MLP controller)
+//   k_compact    Step 1b: windows with key <= tau -> work list, the rest -> next pool
+//                (warp ballot / prefix compaction, structure-of-arrays copies)
+//   k_propagate  Step 2, Algorithm 2: FP64 unfolding, endpoint / occupancy events,
+//                one angle one split, children, Xin-Wang filter
+//   k_fan        Step 2, Fig. `fig:propagation`(c): windows from improved pseudo-sources
+//   sort         Step 3, Algorithm 3: radix sort of the new windows by edge (radix.cu)
+//   k_append     Step 3/4: gap-free append in edge order with per-edge trimming and a
+//                re-filter against the updated distances
+//   k_finish     loop control (Algorithm 1's "until all windows are processed")
+// Events of Algorithm 4 are applied as they are produced: the vertex distance is an
+// atomicMin on the ordered 64-bit image of the nonnegative double, which keeps exactly
+// the first event of Algorithm 4's (key, value) order; angle_split is one packed 64-bit
+// word per half-edge (rounded-up distance | crossing position), also updated by atomicMin.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "pch_host.h"
+#include "radix.cuh"
+#include "solver.cuh"
+
+namespace pch {
+
+// ====================================================================== device helpers
+__device__ __forceinline__ int he_next(int h) { return 3 * (h / 3) + (h % 3 + 1) % 3; }
+
+__device__ __forceinline__ double ldg_dist(const unsigned long long* g, unsigned v) {
+    return bitsd(__ldcg(g + v));
+}
+
+// Pack a (distance to v2, crossing position on the edge) pair for angle_split: the
+// distance is rounded UP to 40 significant bits (so a stored value never understates the
+// window's distance) and the crossing position x/L quantised to 24 bits.
+__device__ __forceinline__ unsigned long long pack_angle(double D, double xs, double iL) {
+    unsigned long long b = dbits(D);
+    if (b & kAngleXMask) b = (b | kAngleXMask) + 1ull;
+    double q = floor(xs * iL * (double)(1 << kAngleXBits));
+    q = fmin(fmax(q, 0.0), (double)kAngleXMask);
+    return (b & ~kAngleXMask) | (unsigned long long)q;
+}
+
+struct WarpScan {
+    int excl, total;
+};
+__device__ __forceinline__ WarpScan warp_scan(int x) {
+    const int lane = threadIdx.x & 31;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    return {incl - x, __shfl_sync(0xffffffffu, incl, 31)};
+}
+
+// Warp-aggregated reservation of `x` slots per lane on counter `c`; returns the lane's base.
+__device__ __forceinline__ int warp_reserve(int* c, int x) {
+    WarpScan s = warp_scan(x);
+    int base = 0;
+    if ((threadIdx.x & 31) == 31 && s.total) base = atomicAdd(c, s.total);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    return base + s.excl;
+}
+
+__device__ __forceinline__ void warp_add_ull(unsigned long long* c, int x) {
+    int t = warp_scan(x).total;
+    if ((threadIdx.x & 31) == 0 && t) atomicAdd(c, (unsigned long long)t);
+}
+
+// Distance event (Algorithm 2, Algorithm 4): min into geod_dist; a pseudo-source vertex
+// whose distance dropped gets one fan request per iteration.
+__device__ __forceinline__ void vertex_event(const Inst& I, int inst, unsigned vf, double D, double& gcache,
+                                             unsigned stamp_val, int2* req, int* n_req, int req_cap, int* err) {
+    if (!(D < gcache)) return;
+    unsigned v = vf & ~kPseudoBit;
+    unsigned long long nb = dbits(D);
+    unsigned long long old = atomicMin(I.g + v, nb);
+    if (nb < old) {
+        gcache = D;
+        if (vf & kPseudoBit) {
+            if (atomicExch(I.stamp + v, stamp_val) != stamp_val) {
+                int slot = atomicAdd(n_req, 1);
+                if (slot < req_cap) req[slot] = make_int2(inst, (int)v);
+                else atomicOr(err, kErrReqFull);
+            }
+        }
+    } else {
+        gcache = bitsd(old);
+    }
+}
+
+__device__ __forceinline__ int hist_bin(double key, double ref, double ilbar) {
+    float t = (float)((key - ref) * ilbar);
+    t = fmaxf(t, 0.f);
+    float b = kBinsPerOctave * __log2f(1.f + kBinScale * t);
+    int bi = (int)b;
+    return bi < 0 ? 0 : (bi >= kBins ? kBins - 1 : bi);
+}
+
+__device__ __forceinline__ double bin_upper(int b, double ref, double lbar) {
+    return ref + lbar * (exp2((double)(b + 1) / (double)kBinsPerOctave) - 1.0) / (double)kBinScale;
+}
+
+// Writes of windows into the next pool also feed the next iteration's selection
+// statistics: per-instance histogram (relative to ctl.ref), minimum key and count.
+struct PoolStats {
+    unsigned* sh_hist;   // shared-memory histogram (n_inst <= kShHistInst) or nullptr
+    unsigned* g_hist;
+    int n_inst;
+};
+constexpr int kShHistInst = 8;
+
+__device__ __forceinline__ void pool_stat(const Work& w, const PoolStats& ps, int inst, double key, bool on) {
+    // minimum key per instance: warp-reduce when the warp holds a single instance
+    const unsigned full = 0xffffffffu;
+    unsigned long long kb = on ? dbits(key) : ~0ull;
+    int inst0 = __shfl_sync(full, inst, 0);
+    bool uniform = __all_sync(full, !on || inst == inst0);
+    if (uniform) {
+        unsigned long long m = kb;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long t = __shfl_xor_sync(full, m, o);
+            m = t < m ? t : m;
+        }
+        int cntw = __popc(__ballot_sync(full, on));
+        if ((threadIdx.x & 31) == 0 && cntw) {
+            atomicMin(&w.ctl[inst0].kmin, m);
+            atomicAdd(&w.ctl[inst0].n_next, cntw);
+        }
+    } else if (on) {
+        atomicMin(&w.ctl[inst].kmin, kb);
+        atomicAdd(&w.ctl[inst].n_next, 1);
+    }
+    if (on) {
+        const InstCtl& c = w.ctl[inst];
+        int b = hist_bin(key, c.ref, w.inst[inst].ilbar);
+        if (ps.sh_hist) atomicAdd(&ps.sh_hist[inst * kBins + b], 1u);
+        else atomicAdd(&ps.g_hist[inst * kBins + b], 1u);
+    }
+}
+
+__device__ __forceinline__ void load_win(const WinSoA& s, int i, int& he, int& inst, double& d, double& A, double& B,
+                                         double& px, double& py, double& key) {
+    he = s.he[i]; inst = s.inst[i]; d = s.d[i]; A = s.A[i]; B = s.B[i]; px = s.px[i]; py = s.py[i]; key = s.key[i];
+}
+__device__ __forceinline__ void store_win(const WinSoA& s, int i, int he, int inst, double d, double A, double B,
+                                          double px, double py, double key) {
+    s.he[i] = he; s.inst[i] = inst; s.d[i] = d; s.A[i] = A; s.B[i] = B; s.px[i] = px; s.py[i] = py; s.key[i] = key;
+}
+
+// ====================================================================== init
+__global__ void k_fill_inf(unsigned long long* g, long long n) {
+    const unsigned long long inf = 0x7FF0000000000000ull;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        g[i] = inf;
+}
+
+// Algorithm 1, initialisation: geod_dist = 0 at the sources; a window on every edge
+// opposite a source (issued as the source's fan request); for a point inside a face,
+// one window on each edge of the face and the three corner distances.
+__global__ void k_init_sources(Work w, const SrcDev* __restrict__ srcs, int n_src) {
+    Counters* cnt = w.cnt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_src; i += gridDim.x * blockDim.x) {
+        SrcDev s = srcs[i];
+        const Inst& I = w.inst[s.inst];
+        if (s.kind == 0) {
+            I.g[s.vertex] = 0ull;
+            if (atomicExch(I.stamp + s.vertex, 1u) != 1u) {
+                int slot = atomicAdd(&cnt->n_req, 1);
+                if (slot < w.req_cap) w.req[0][slot] = make_int2(s.inst, s.vertex);
+                else atomicOr(&cnt->error, kErrReqFull);
+            }
+        }
+    }
+}
+
+// Face-point sources (one thread each, after k_init_sources): corner distances and the
+// three windows, written to the child arena of iteration 0.
+__global__ void k_init_face_sources(Work w, const SrcDev* __restrict__ srcs, int n_src) {
+    Counters* cnt = w.cnt;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_src; i += gridDim.x * blockDim.x) {
+        SrcDev s = srcs[i];
+        if (s.kind != 1) continue;
+        const Inst& I = w.inst[s.inst];
+        for (int k = 0; k < 3; ++k) {
+            int h = 3 * s.face + k;
+            HERec R = I.rec[h];
+            // barycentric weights of h's end vertex and apex (its start vertex sits at 0)
+            double b1 = s.bary[(k + 1) % 3], b2 = s.bary[(k + 2) % 3];
+            double x = b1 * R.L + b2 * R.xc, y = b2 * R.yc;        // point in h's frame
+            double dstart = sqrt(x * x + y * y);
+            double gc = ldg_dist(I.g, R.v0 & ~kPseudoBit);
+            vertex_event(I, s.inst, R.v0, dstart, gc, 1u, w.req[0], &cnt->n_req, w.req_cap, &cnt->error);
+            if (R.twin < 0) continue;
+            // window on twin(h) = (v1 -> v0): point at (L - x, -y), interval [0, L]
+            double px = R.L - x, py = -y;
+            double key = px < 0 ? sqrt(px * px + py * py)
+                                : (px > R.L ? sqrt((px - R.L) * (px - R.L) + py * py) : -py);
+            int slot = atomicAdd(&cnt->n_child, 1);
+            if (slot < w.arena_cap) store_win(w.arena, slot, R.twin, s.inst, 0.0, 0.0, R.L, px, py, key);
+        }
+    }
+}
+
+// ====================================================================== Step 1: selection
+// Per instance: the plain control selects the k nearest windows (Section 4.2, Step 1)
+// through the key histogram: tau = upper edge of the first bin where the cumulative
+// count reaches k.  Also rolls the histogram reference and the running minimum.
+__global__ void k_tau(Work w, int control, const float* __restrict__ mlp) {
+    __shared__ unsigned sh[kBins];
+    __shared__ float feat[kFeatures];
+    __shared__ float hb0[kHidden], hb1[kHidden];
+    __shared__ float y;
+    Counters* cnt = w.cnt;
+    if (cnt->halt) return;
+    const int it = cnt->iter;
+    const unsigned* hist = w.hist[it & 1];
+    unsigned* hist_nx = w.hist[(it + 1) & 1];
+    for (int inst = blockIdx.x; inst < w.n_inst; inst += gridDim.x) {
+        InstCtl& c = w.ctl[inst];
+        const int np = c.n_next;
+        for (int b = threadIdx.x; b < kBins; b += blockDim.x) sh[b] = hist[inst * kBins + b];
+        __syncthreads();
+        const bool learned = control == PCH_CONTROL_LEARNED && mlp != nullptr && np > 0;
+        if ((learned || w.trace) && threadIdx.x == 0) controller_features(c, w.inst[inst], sh, np, it, feat);
+        __syncthreads();
+        if (learned) mlp_forward_block(mlp, feat, hb0, hb1, &y);
+        if (threadIdx.x == 0) {
+            double tau;
+            const double ref = c.ref;
+            const double lbar = w.inst[inst].lbar;
+            long long k = c.k_target;
+            if (learned) {
+                c.ctl_out = y;
+                // y = log2 of the fraction of pending windows to select; plain k otherwise
+                if (isfinite(y) && y <= 0.f && y >= -24.f) {
+                    long long kk = (long long)ceil(exp2((double)y) * np);
+                    k = kk < 1 ? 1 : kk;
+                }
+            }
+            if (np == 0) {
+                tau = -INFINITY;
+            } else if ((long long)np <= k) {
+                tau = INFINITY;
+            } else {
+                long long run = 0;
+                int b = 0;
+                for (; b < kBins; ++b) {
+                    run += sh[b];
+                    if (run >= k) break;
+                }
+                tau = b >= kBins - 1 ? INFINITY : bin_upper(b, ref, lbar);
+            }
+            if (w.trace && np > 0) {
+                int row = atomicAdd(w.trace_rows, 1);
+                if (row < w.trace_cap) {
+                    float* f = w.trace + (size_t)row * (kFeatures + 2);
+                    for (int j = 0; j < kFeatures; ++j) f[j] = feat[j];
+                    f[kFeatures] = (float)log2(fmin(1.0, (double)k / (double)np));
+                    f[kFeatures + 1] = (float)inst;
+                }
+            }
+            c.tau = tau;
+            c.n_pending = np;
+            c.n_next = 0;
+            if (c.kmin != ~0ull) c.ref = bitsd(c.kmin);   // min key of the current pool
+            c.kmin = ~0ull;
+        }
+        for (int b = threadIdx.x; b < kBins; b += blockDim.x) hist_nx[inst * kBins + b] = 0u;
+        __syncthreads();
+    }
+}
+
+// Compaction: selected windows to the work list, the rest to the next pool.
+__global__ void __launch_bounds__(256) k_compact(Work w) {
+    __shared__ unsigned sh_hist[kShHistInst * kBins];
+    Counters* cnt = w.cnt;
+    if (cnt->halt) return;
+    const int it = cnt->iter;
+    const WinSoA cur = w.pool[it & 1], nxt = w.pool[(it + 1) & 1];
+    const int n = min(cnt->n_pending, w.pool_cap);
+    PoolStats ps{w.n_inst <= kShHistInst ? sh_hist : nullptr, w.hist[(it + 1) & 1], w.n_inst};
+    if (ps.sh_hist) {
+        for (int j = threadIdx.x; j < w.n_inst * kBins; j += blockDim.x) sh_hist[j] = 0u;
+        __syncthreads();
+    }
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        int i = base + threadIdx.x;
+        bool valid = i < n;
+        int he = 0, inst = 0;
+        double d = 0, A = 0, B = 0, px = 0, py = 0, key = 0;
+        if (valid) load_win(cur, i, he, inst, d, A, B, px, py, key);
+        bool sel = valid && key <= w.ctl[inst].tau;
+        int slot = warp_reserve(&cnt->n_sel, sel ? 1 : 0);
+        if (sel && slot >= w.sel_cap) sel = false;   // work list full: stays pending
+        if (sel) store_win(w.sel, slot, he, inst, d, A, B, px, py, key);
+        bool rest = valid && !sel;
+        int rslot = warp_reserve(&cnt->n_rest, rest ? 1 : 0);
+        if (rest) store_win(nxt, rslot, he, inst, d, A, B, px, py, key);
+        pool_stat(w, ps, inst, key, rest);
+    }
+    if (ps.sh_hist) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < w.n_inst * kBins; j += blockDim.x)
+            if (sh_hist[j]) atomicAdd(&ps.g_hist[j], sh_hist[j]);
+    }
+}
+
+// ====================================================================== Step 2: propagation
+struct ChildOut {
+    int he;
+    double A, B, px, py, key;
+};
+
+// Ray from I' through P' (child frame, both below the child's x axis) meets the axis at
+// X; returns x(X) and |I X| = t |I P|.  Clamped to [0, Lc] with |IX| recomputed there.
+__device__ __forceinline__ void ray_hit(double Ipx, double Ipy, double Ppx, double Ppy, double IP, double Lc,
+                                        double& xh, double& IX) {
+    double den = Ppy - Ipy;
+    double t = -Ipy / den;
+    xh = Ipx + t * (Ppx - Ipx);
+    IX = t * IP;
+    if (!(den > 0.0) || !(xh >= 0.0 && xh <= Lc)) {
+        xh = den > 0.0 ? fmin(fmax(xh, 0.0), Lc) : (Ppx > Ipx ? Lc : 0.0);
+        if (!(xh == xh)) xh = 0.0;
+        double dx = xh - Ipx;
+        IX = sqrt(dx * dx + Ipy * Ipy);
+    }
+}
+
+__device__ __forceinline__ double child_key(double d, double a, double b, double Ipx, double Ipy, double IA,
+                                            double IB) {
+    return d + (Ipx < a ? IA : (Ipx > b ? IB : -Ipy));
+}
+
+__global__ void __launch_bounds__(256) k_propagate(Work w) {
+    Counters* cnt = w.cnt;
+    if (cnt->halt) return;
+    const int it = cnt->iter;
+    const int n = min(cnt->n_sel, w.sel_cap);
+    int2* req = w.req[it & 1];
+    const unsigned stamp_val = (unsigned)it + 1u;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        ChildOut c[2];
+        int nc = 0, inst = 0;
+        double d = 0.0;
+        bool prop = false;
+        if (i < n) {
+            const int h = w.sel.he[i];
+            inst = w.sel.inst[i];
+            d = w.sel.d[i];
+            const double A = w.sel.A[i], B = w.sel.B[i], px = w.sel.px[i], py = w.sel.py[i];
+            const Inst& I = w.inst[inst];
+            const HERec R = I.rec[h];
+            const double L = R.L;
+            double g0 = ldg_dist(I.g, R.v0 & ~kPseudoBit);
+            double g1 = ldg_dist(I.g, R.v1 & ~kPseudoBit);
+            double g2 = ldg_dist(I.g, R.v2 & ~kPseudoBit);
+            const double py2 = py * py;
+            const double ax = A - px, bx = B - px;
+            const double IA = sqrt(ax * ax + py2), IB = sqrt(bx * bx + py2);
+            // Xin-Wang endpoint tests against the current distances: the window is
+            // useless if the path via v0 beats it at B, or the path via v1 at A.
+            if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)))) {
+                prop = true;
+                const double tol = kEpsSnap * L;
+                // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
+                if (A <= tol) {
+                    double D0 = d + (A == 0.0 ? IA : sqrt(px * px + py2));
+                    vertex_event(I, inst, R.v0, D0, g0, stamp_val, req, &cnt->n_req, w.req_cap, &cnt->error);
+                }
+                if (B >= L - tol) {
+                    double q = L - px;
+                    double D1 = d + (B == L ? IB : sqrt(q * q + py2));
+                    vertex_event(I, inst, R.v1, D1, g1, stamp_val, req, &cnt->n_req, w.req_cap, &cnt->error);
+                }
+                // occupancy of v2: the ray I -> v2 crosses e at xs
+                const double xc = R.xc, yc = R.yc;
+                const double xs = px + (xc - px) * (-py) / (yc - py);
+                const bool occ = (xs >= A - tol) && (xs <= B + tol);
+                const double xcl = fmin(fmax(xs, A), B);
+                bool left, right;
+                double Iv2 = 0.0;
+                if (occ) {
+                    const double dx = xc - px, dy = yc - py;
+                    Iv2 = sqrt(dx * dx + dy * dy);
+                    const double D2 = d + Iv2;
+                    // one angle one split (Fig. `fig:filter`(a)) against angle_split[h]
+                    unsigned long long* ap = I.ang + h;
+                    const unsigned long long aw = __ldcg(ap);
+                    bool win = aw == kEmptyAngle || D2 < bitsd(aw & ~kAngleXMask);
+                    if (win) {
+                        left = right = true;
+                        atomicMin(ap, pack_angle(D2, xs, R.iL));
+                    } else {
+                        // loser: keep the child on its own side of the winner's ray
+                        const double q = (double)(aw & kAngleXMask);
+                        const double sc = L * (1.0 / (double)(1 << kAngleXBits));
+                        left = xs < q * sc - tol;
+                        right = xs > (q + 1.0) * sc + tol;
+                        if (!left && !right) left = right = true;
+                    }
+                    vertex_event(I, inst, R.v2, D2, g2, stamp_val, req, &cnt->n_req, w.req_cap, &cnt->error);
+                    if (B - xcl <= kEpsTiny * L) right = false;
+                    if (xcl - A <= kEpsTiny * L) left = false;
+                } else {
+                    right = xs < A;
+                    left = !right;
+                }
+                if (right && R.tw1 >= 0) {
+                    // child on edge v2 -> v1 (twin of next(h)): frame origin v2
+                    const double L1 = R.L1;
+                    const double ux = (L - xc) * R.iL1, uy = -yc * R.iL1;
+                    const double rx = px - xc, ry = py - yc;
+                    const double Ipx = rx * ux + ry * uy, Ipy = ux * ry - uy * rx;
+                    double a, IAc, b, IBc;
+                    if (occ) {
+                        a = 0.0;
+                        IAc = Iv2;
+                    } else {
+                        const double qx = A - xc;
+                        ray_hit(Ipx, Ipy, qx * ux - yc * uy, -ux * yc - uy * qx, IA, L1, a, IAc);
+                    }
+                    {
+                        const double qx = B - xc;
+                        ray_hit(Ipx, Ipy, qx * ux - yc * uy, -ux * yc - uy * qx, IB, L1, b, IBc);
+                    }
+                    if (b - a > kEpsTiny * L1) {
+                        const double Xx = xc + b * ux, Xy = yc + b * uy;      // X_B in h's frame
+                        const double v0X = sqrt(Xx * Xx + Xy * Xy);
+                        // Xin-Wang filter (Fig. `fig:filter`(b)) on the new window
+                        if (!(dominated(d + IBc, g2 + b) || dominated(d + IAc, g1 + (L1 - a)) ||
+                              dominated(d + IBc, g0 + v0X))) {
+                            c[nc++] = ChildOut{R.tw1, a, b, Ipx, Ipy, child_key(d, a, b, Ipx, Ipy, IAc, IBc)};
+                        }
+                    }
+                }
+                if (left && R.tw2 >= 0) {
+                    // child on edge v0 -> v2 (twin of prev(h)): frame origin v0
+                    const double L2 = R.L2;
+                    const double ux = xc * R.iL2, uy = yc * R.iL2;
+                    const double Ipx = px * ux + py * uy, Ipy = ux * py - uy * px;
+                    double a, IAc, b, IBc;
+                    ray_hit(Ipx, Ipy, A * ux, -uy * A, IA, L2, a, IAc);
+                    if (occ) {
+                        b = L2;
+                        IBc = Iv2;
+                    } else {
+                        ray_hit(Ipx, Ipy, B * ux, -uy * B, IB, L2, b, IBc);
+                    }
+                    if (b - a > kEpsTiny * L2) {
+                        const double Xx = a * ux - L, Xy = a * uy;            // X_A - v1 in h's frame
+                        const double v1X = sqrt(Xx * Xx + Xy * Xy);
+                        if (!(dominated(d + IBc, g0 + b) || dominated(d + IAc, g2 + (L2 - a)) ||
+                              dominated(d + IAc, g1 + v1X))) {
+                            c[nc++] = ChildOut{R.tw2, a, b, Ipx, Ipy, child_key(d, a, b, Ipx, Ipy, IAc, IBc)};
+                        }
+                    }
+                }
+            }
+        }
+        int slot = warp_reserve(&cnt->n_child, nc);
+        for (int j = 0; j < nc; ++j) {
+            int s = slot + j;
+            if (s < w.arena_cap) store_win(w.arena, s, c[j].he, inst, d, c[j].A, c[j].B, c[j].px, c[j].py, c[j].key);
+            else atomicOr(&cnt->error, kErrPoolFull);
+        }
+        warp_add_ull(&cnt->propagated, prop ? 1 : 0);
+    }
+}
+
+// Pseudo-source fans (Fig. `fig:propagation`(c)): for every vertex whose distance dropped
+// this iteration, one window on each edge of its one-ring opposite it, with I = the
+// vertex and d = its distance.  Boundary edges get their endpoint events instead.
+__global__ void k_fan(Work w) {
+    Counters* cnt = w.cnt;
+    if (cnt->halt) return;
+    const int it = cnt->iter;
+    const int nreq = min(cnt->n_req, w.req_cap);
+    const int2* req = w.req[it & 1];
+    int2* req_nx = w.req[(it + 1) & 1];
+    const unsigned stamp_nx = (unsigned)it + 2u;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreq; r += gridDim.x * blockDim.x) {
+        const int inst = req[r].x;
+        const unsigned v = (unsigned)req[r].y;
+        const Inst& I = w.inst[inst];
+        const double D = ldg_dist(I.g, v);
+        const int s = I.vstart[v], e = I.vstart[v + 1];
+        const int deg = e - s;
+        const int base = atomicAdd(&cnt->n_child, deg);
+        if (base + deg > w.arena_cap) {
+            // no room this iteration: mark the reserved slots empty, retry next iteration
+            for (int j = base; j < min(base + deg, w.arena_cap); ++j) w.arena.he[j] = -1;
+            atomicExch(I.stamp + v, stamp_nx);
+            int slot = atomicAdd(&cnt->n_req_next, 1);
+            if (slot < w.req_cap) req_nx[slot] = make_int2(inst, (int)v);
+            else atomicOr(&cnt->error, kErrReqFull);
+            continue;
+        }
+        for (int j = 0; j < deg; ++j) {
+            const int hv = I.vlist[s + j];
+            const int o = he_next(hv);                 // edge (a -> b) opposite v
+            const HERec Ro = I.rec[o];
+            const double va = Ro.L2, vb = Ro.L1;       // |v a|, |v b|
+            double ga = ldg_dist(I.g, Ro.v0 & ~kPseudoBit), gb = ldg_dist(I.g, Ro.v1 & ~kPseudoBit);
+            const int slot = base + j;
+            if (Ro.twin < 0) {
+                vertex_event(I, inst, Ro.v0, D + va, ga, stamp_nx, req_nx, &cnt->n_req_next, w.req_cap, &cnt->error);
+                vertex_event(I, inst, Ro.v1, D + vb, gb, stamp_nx, req_nx, &cnt->n_req_next, w.req_cap, &cnt->error);
+                w.arena.he[slot] = -1;
+                continue;
+            }
+            const double Lo = Ro.L;
+            // window on twin(o) = (b -> a): I = v at (Lo - xc, -yc), interval [0, Lo]
+            if (dominated(D + va, gb + Lo) || dominated(D + vb, ga + Lo)) {
+                w.arena.he[slot] = -1;
+                continue;
+            }
+            const double px = Lo - Ro.xc, py = -Ro.yc;
+            const double key = D + (px < 0.0 ? vb : (px > Lo ? va : Ro.yc));
+            store_win(w.arena, slot, Ro.twin, inst, D, 0.0, Lo, px, py, key);
+        }
+    }
+}
+
+// ====================================================================== Step 3/4: append
+__global__ void __launch_bounds__(256) k_append(Work w, const unsigned* __restrict__ keys, const int* __restrict__ vals,
+                                                int trim) {
+    __shared__ unsigned sh_hist[kShHistInst * kBins];
+    Counters* cnt = w.cnt;
+    if (cnt->halt) return;
+    const int it = cnt->iter;
+    const WinSoA nxt = w.pool[(it + 1) & 1];
+    const int n = min(cnt->n_child, w.arena_cap);
+    const int n_rest = cnt->n_rest;
+    PoolStats ps{w.n_inst <= kShHistInst ? sh_hist : nullptr, w.hist[(it + 1) & 1], w.n_inst};
+    if (ps.sh_hist) {
+        for (int j = threadIdx.x; j < w.n_inst * kBins; j += blockDim.x) sh_hist[j] = 0u;
+        __syncthreads();
+    }
+    constexpr int kTrimReach = 4;
+    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
+        const int i = base + threadIdx.x;
+        unsigned k = i < n ? keys[i] : ~0u;
+        bool keep = k != ~0u;
+        int he = 0, inst = 0;
+        double d = 0, A = 0, B = 0, px = 0, py = 0, key = 0;
+        int trimmed = 0;
+        if (keep) {
+            load_win(w.arena, vals[i], he, inst, d, A, B, px, py, key);
+            const Inst& I = w.inst[inst];
+            const HERec R = I.rec[he];
+            // re-filter against the distances after this iteration's events (the window
+            // is nowhere closer than `key`)
+            double g0 = ldg_dist(I.g, R.v0 & ~kPseudoBit), g1 = ldg_dist(I.g, R.v1 & ~kPseudoBit);
+            if (dominated(key, g0 + B) || dominated(key, g1 + (R.L - A))) keep = false;
+            // per-edge trimming: a window on the same edge that covers [A, B] and is
+            // everywhere shorter than this window's nearest point makes it useless
+            if (keep && trim) {
+                for (int dir = -1; dir <= 1 && keep; dir += 2) {
+                    for (int s = 1; s <= kTrimReach && keep; ++s) {
+                        int j = i + dir * s;
+                        if (j < 0 || j >= n || keys[j] != k) break;
+                        int jj = vals[j];
+                        double A2 = w.arena.A[jj], B2 = w.arena.B[jj];
+                        if (!(A2 <= A && B2 >= B)) continue;
+                        double d2 = w.arena.d[jj], px2 = w.arena.px[jj], py2 = w.arena.py[jj];
+                        double ea = A - px2, eb = B - px2;
+                        double mx = d2 + sqrt(fmax(ea * ea, eb * eb) + py2 * py2);
+                        if (dominated(key, mx)) { keep = false; trimmed = 1; }
+                    }
+                }
+            }
+        }
+        int slot = warp_reserve(&cnt->n_app, keep ? 1 : 0);
+        if (keep) {
+            int pos = n_rest + slot;
+            if (pos < w.pool_cap) store_win(nxt, pos, he, inst, d, A, B, px, py, key);
+            else atomicOr(&cnt->error, kErrPoolFull);
+        }
+        pool_stat(w, ps, inst, key, keep);
+        warp_add_ull(&cnt->trimmed, trimmed);
+        warp_add_ull(&cnt->created, keep ? 1 : 0);
+    }
+    if (ps.sh_hist) {
+        __syncthreads();
+        for (int j = threadIdx.x; j < w.n_inst * kBins; j += blockDim.x)
+            if (sh_hist[j]) atomicAdd(&ps.g_hist[j], sh_hist[j]);
+    }
+}
+
+// ====================================================================== loop control
+__global__ void k_finish(Work w, cudaGraphConditionalHandle handle, int use_cond, long long max_iters) {
+    Counters* c = w.cnt;
+    if (!c->halt) {
+        int np = c->n_rest + c->n_app;
+        const float ratio = c->n_sel > 0 ? (float)c->n_app / (float)c->n_sel : 0.f;
+        for (int i = 0; i < w.n_inst; ++i) w.ctl[i].last_ratio = ratio;
+        c->n_pending = np;
+        if ((unsigned long long)np > c->peak_pending) c->peak_pending = (unsigned long long)np;
+        c->n_req = min(c->n_req_next, w.req_cap);
+        c->n_req_next = 0;
+        c->n_rest = 0;
+        c->n_sel = 0;
+        c->n_child = 0;
+        c->n_app = 0;
+        c->iter += 1;
+        c->done = (np == 0 && c->n_req == 0) ? 1 : 0;
+        if (!c->done && c->iter >= max_iters) c->error |= kErrIter;
+        // stop for the host: finished, an error, or the pool may not hold one more iteration
+        c->halt = (c->done || c->error != 0 || np + w.arena_cap > w.pool_cap) ? 1 : 0;
+    }
+    if (use_cond) cudaGraphSetConditional(handle, c->halt ? 0u : 1u);
+}
+
+__global__ void k_copy_out(const unsigned long long* __restrict__ g, double* out, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) out[i] = bitsd(g[i]);
+}
+
+__global__ void k_min_into(const unsigned long long* __restrict__ g, unsigned long long* acc, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (g[i] < acc[i]) acc[i] = g[i];
+}
+
+// ====================================================================== host side
+struct Alloc {
+    std::vector<void*> ptrs;
+    size_t bytes = 0;
+    template <class T>
+    cudaError_t get(T** p, size_t n) {
+        if (n == 0) n = 1;
+        cudaError_t e = cudaMalloc((void**)p, sizeof(T) * n);
+        if (e == cudaSuccess) { ptrs.push_back(*p); bytes += sizeof(T) * n; }
+        return e;
+    }
+    void release() {
+        for (void* p : ptrs) cudaFree(p);
+        ptrs.clear();
+        bytes = 0;
+    }
+};
+
+struct GraphKey {
+    SolveCfg cfg;
+    Work w;
+};
+
+struct Workspace {
+    int device = 0;
+    Alloc pools;            // pools, arena, sort buffers, requests (sized by caps)
+    Alloc inst_mem;         // g / angle_split / stamps (sized by the instances)
+    Alloc fixed;            // counters, tables
+    Work w{};
+    int pool_cap = 0, sel_cap = 0, arena_cap = 0, req_cap = 0;
+    long long g_cap = 0, ang_cap = 0, st_cap = 0;
+    int inst_cap = 0;
+    unsigned long long* g_all = nullptr;
+    unsigned long long* ang_all = nullptr;
+    unsigned* stamp_all = nullptr;
+    Counters* cnt_host = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    // graph cache: rebuilt when pointers or launch parameters change
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    GraphKey gkey{};
+    float* trace_buf = nullptr;
+    int* trace_rows = nullptr;
+    int trace_cap = 0;
+    bool trace_on = false;
+};
+
+void destroy_workspace(Workspace* ws) {
+    if (!ws) return;
+    if (ws->exec) cudaGraphExecDestroy(ws->exec);
+    if (ws->graph) cudaGraphDestroy(ws->graph);
+    ws->pools.release();
+    ws->inst_mem.release();
+    ws->fixed.release();
+    if (ws->cnt_host) cudaFreeHost(ws->cnt_host);
+    for (auto& e : ws->ev) if (e) cudaEventDestroy(e);
+    delete ws;
+}
+
+static void drop_graph(Workspace* ws) {
+    if (ws->exec) cudaGraphExecDestroy(ws->exec);
+    if (ws->graph) cudaGraphDestroy(ws->graph);
+    ws->exec = nullptr;
+    ws->graph = nullptr;
+}
+
+static cudaError_t alloc_soa(Alloc& a, WinSoA& s, int cap) {
+    cudaError_t e;
+    if ((e = a.get(&s.he, cap))) return e;
+    if ((e = a.get(&s.inst, cap))) return e;
+    if ((e = a.get(&s.d, cap))) return e;
+    if ((e = a.get(&s.A, cap))) return e;
+    if ((e = a.get(&s.B, cap))) return e;
+    if ((e = a.get(&s.px, cap))) return e;
+    if ((e = a.get(&s.py, cap))) return e;
+    return a.get(&s.key, cap);
+}
+
+static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap) {
+    int arena_cap = 6 * sel_cap;
+    if (pool_cap < 2 * arena_cap) pool_cap = 2 * arena_cap;
+    if (sel_cap <= ws->sel_cap && pool_cap <= ws->pool_cap) return PCH_OK;
+    sel_cap = std::max(sel_cap, ws->sel_cap);
+    pool_cap = std::max(pool_cap, ws->pool_cap);
+    arena_cap = 6 * sel_cap;
+    const int req_cap = 4 * sel_cap + (1 << 20);
+    const int sort_blocks = 2 * sm_count();
+    drop_graph(ws);
+    Work& w = ws->w;
+    Work nw = w;
+    Alloc fresh;
+    cudaError_t e = cudaSuccess;
+    if (!e) e = alloc_soa(fresh, nw.pool[0], pool_cap);
+    if (!e) e = alloc_soa(fresh, nw.pool[1], pool_cap);
+    if (!e) e = alloc_soa(fresh, nw.sel, sel_cap);
+    if (!e) e = alloc_soa(fresh, nw.arena, arena_cap);
+    if (!e) e = fresh.get(&nw.req[0], req_cap);
+    if (!e) e = fresh.get(&nw.req[1], req_cap);
+    if (!e) e = fresh.get(&nw.sort_key[0], arena_cap);
+    if (!e) e = fresh.get(&nw.sort_key[1], arena_cap);
+    if (!e) e = fresh.get(&nw.sort_val[0], arena_cap);
+    if (!e) e = fresh.get(&nw.sort_val[1], arena_cap);
+    if (!e) e = fresh.get(&nw.sort_hist, (size_t)kRsDigits * sort_blocks);
+    if (e) {
+        fresh.release();
+        return set_error(e == cudaErrorMemoryAllocation ? PCH_ERR_OOM : PCH_ERR_CUDA, "workspace allocation: %s",
+                         cudaGetErrorString(e));
+    }
+    if (ws->pool_cap > 0) {
+        // growth between iterations: keep the pending pools and the fan requests
+        const size_t n = (size_t)ws->pool_cap;
+        for (int p = 0; p < 2; ++p) {
+            cudaMemcpy(nw.pool[p].he, w.pool[p].he, n * 4, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].inst, w.pool[p].inst, n * 4, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].d, w.pool[p].d, n * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].A, w.pool[p].A, n * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].B, w.pool[p].B, n * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].px, w.pool[p].px, n * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].py, w.pool[p].py, n * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].key, w.pool[p].key, n * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.req[p], w.req[p], sizeof(int2) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
+        }
+        e = cudaDeviceSynchronize();
+        if (e) { fresh.release(); return set_error(PCH_ERR_CUDA, "pool growth copy: %s", cudaGetErrorString(e)); }
+    }
+    ws->pools.release();
+    ws->pools = fresh;
+    w = nw;
+    ws->pool_cap = w.pool_cap = pool_cap;
+    ws->sel_cap = w.sel_cap = sel_cap;
+    ws->arena_cap = w.arena_cap = arena_cap;
+    ws->req_cap = w.req_cap = req_cap;
+    w.sort_blocks = sort_blocks;
+    return PCH_OK;
+}
+
+struct InstSpec {
+    pch_mesh* m;
+    long long goff, aoff;
+    int k_src_begin, k_src_end;
+};
+
+static pch_status ensure_workspace(pch_mesh* owner, Workspace** out) {
+    if (!owner->ws) {
+        Workspace* ws = new Workspace();
+        cudaGetDevice(&ws->device);
+        if (cudaMallocHost(&ws->cnt_host, sizeof(Counters)) != cudaSuccess) {
+            delete ws;
+            return set_error(PCH_ERR_OOM, "pinned counter allocation failed");
+        }
+        cudaEventCreate(&ws->ev[0]);
+        cudaEventCreate(&ws->ev[1]);
+        if (ws->fixed.get(&ws->w.cnt, 1) != cudaSuccess) {
+            destroy_workspace(ws);
+            return set_error(PCH_ERR_OOM, "counter allocation failed");
+        }
+        owner->ws = ws;
+    }
+    *out = owner->ws;
+    return PCH_OK;
+}
+
+static pch_status ensure_instances(Workspace* ws, int n_inst, long long g_total, long long a_total) {
+    if (n_inst <= ws->inst_cap && g_total <= ws->g_cap && a_total <= ws->ang_cap) return PCH_OK;
+    drop_graph(ws);
+    ws->inst_mem.release();
+    Work& w = ws->w;
+    int ic = std::max(n_inst, ws->inst_cap);
+    long long gc = std::max(g_total, ws->g_cap), ac = std::max(a_total, ws->ang_cap);
+    cudaError_t e = cudaSuccess;
+    if (!e) e = ws->inst_mem.get(&ws->g_all, gc);
+    if (!e) e = ws->inst_mem.get(&ws->ang_all, ac);
+    if (!e) e = ws->inst_mem.get(&ws->stamp_all, gc);
+    if (!e) e = ws->inst_mem.get(&w.inst, ic);
+    if (!e) e = ws->inst_mem.get(&w.ctl, ic);
+    if (!e) e = ws->inst_mem.get(&w.hist[0], (size_t)ic * kBins);
+    if (!e) e = ws->inst_mem.get(&w.hist[1], (size_t)ic * kBins);
+    if (e) {
+        ws->inst_mem.release();
+        ws->inst_cap = 0; ws->g_cap = ws->ang_cap = 0;
+        return set_error(e == cudaErrorMemoryAllocation ? PCH_ERR_OOM : PCH_ERR_CUDA, "instance allocation: %s",
+                         cudaGetErrorString(e));
+    }
+    ws->inst_cap = ic;
+    ws->g_cap = gc;
+    ws->ang_cap = ac;
+    return PCH_OK;
+}
+
+static int grid_for(int blocks_per_sm) { return sm_count() * blocks_per_sm; }
+
+// Launch one iteration (all phases).  Returns a CUDA error if a launch failed.
+static cudaError_t launch_iteration(Workspace* ws, cudaStream_t s, const SolveCfg& cfg, cudaGraphConditionalHandle h,
+                                    int use_cond) {
+    Work& w = ws->w;
+    const int tpb = 256;
+    k_tau<<<std::min(w.n_inst, 1024), 256, 0, s>>>(w, cfg.control, cfg.mlp);
+    k_compact<<<grid_for(4), tpb, 0, s>>>(w);
+    k_propagate<<<grid_for(cfg.prop_blocks_per_sm), cfg.prop_threads, 0, s>>>(w);
+    k_fan<<<grid_for(2), 128, 0, s>>>(w);
+    unsigned* kb[2] = {w.sort_key[0], w.sort_key[1]};
+    int* vb[2] = {w.sort_val[0], w.sort_val[1]};
+    int par = launch_sort_children(w.arena, w.inst, &w.cnt->n_child, w.arena_cap, cfg.key_bits, kb, vb, w.sort_hist,
+                                   w.sort_blocks, s);
+    k_append<<<grid_for(4), tpb, 0, s>>>(w, kb[par], vb[par], cfg.trim);
+    k_finish<<<1, 1, 0, s>>>(w, h, use_cond, cfg.max_iters);
+    return cudaGetLastError();
+}
+
+static pch_status build_graph(Workspace* ws, cudaStream_t s, const SolveCfg& cfg) {
+    drop_graph(ws);
+    cudaGraph_t graph;
+    PCH_CUDA(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle handle;
+    cudaError_t e = cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault);
+    if (e) { cudaGraphDestroy(graph); PCH_CUDA(e); }
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = handle;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp);
+    if (e) { cudaGraphDestroy(graph); PCH_CUDA(e); }
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    cudaStream_t cs;
+    PCH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (!e) {
+        for (int u = 0; u < cfg.unroll && !e; ++u) e = launch_iteration(ws, cs, cfg, handle, u == cfg.unroll - 1);
+        cudaGraph_t outg = body;
+        cudaError_t e2 = cudaStreamEndCapture(cs, &outg);
+        if (!e) e = e2;
+    }
+    cudaStreamDestroy(cs);
+    if (e) { cudaGraphDestroy(graph); PCH_CUDA(e); }
+    cudaGraphExec_t exec;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e) { cudaGraphDestroy(graph); PCH_CUDA(e); }
+    ws->graph = graph;
+    ws->exec = exec;
+    (void)s;
+    return PCH_OK;
+}
+
+static pch_status status_from_error(int err) {
+    if (err & kErrIter) return set_error(PCH_ERR_TIMEOUT, "iteration cap reached before all windows were processed");
+    if (err & (kErrPoolFull | kErrReqFull)) return set_error(PCH_ERR_CAPACITY, "window pool capacity exceeded (error %d)", err);
+    return set_error(PCH_ERR_CUDA, "solver error flags %d", err);
+}
+
+// Common driver: instances already described by `specs` and `srcs_dev`.
+static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_in, pch_stats* stats) {
+    SolveCfg cfg = cfg_in;
+    Work& w = ws->w;
+    // iterations
+    PCH_CUDA(cudaEventRecord(ws->ev[0], s));
+    if (cfg.loop == PCH_LOOP_HOST) {
+        for (long long it = 0;; ++it) {
+            PCH_CUDA(launch_iteration(ws, s, cfg, 0, 0));
+            PCH_CUDA(cudaMemcpyAsync(ws->cnt_host, w.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+            PCH_CUDA(cudaStreamSynchronize(s));
+            const Counters& c = *ws->cnt_host;
+            if (c.error || c.done) break;
+            if (c.n_pending + w.arena_cap > w.pool_cap) {
+                pch_status st = ensure_pools(ws, ws->sel_cap, 2 * ws->pool_cap);
+                if (st != PCH_OK) return st;
+                PCH_CUDA(cudaMemsetAsync(&w.cnt->halt, 0, sizeof(int), s));
+            }
+        }
+    } else {
+        while (true) {
+            GraphKey key{};
+            key.cfg = cfg;
+            key.w = w;
+            if (!(ws->exec && std::memcmp(&key, &ws->gkey, sizeof key) == 0)) {
+                pch_status st = build_graph(ws, s, cfg);
+                if (st != PCH_OK) return st;
+                ws->gkey = key;
+            }
+            PCH_CUDA(cudaGraphLaunch(ws->exec, s));
+            PCH_CUDA(cudaMemcpyAsync(ws->cnt_host, w.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+            PCH_CUDA(cudaStreamSynchronize(s));
+            const Counters& c = *ws->cnt_host;
+            if (c.error || c.done) break;
+            if (c.n_pending + w.arena_cap > w.pool_cap) {
+                pch_status st = ensure_pools(ws, ws->sel_cap, 2 * ws->pool_cap);
+                if (st != PCH_OK) return st;
+                PCH_CUDA(cudaMemsetAsync(&w.cnt->halt, 0, sizeof(int), s));
+                continue;
+            }
+        }
+    }
+    PCH_CUDA(cudaEventRecord(ws->ev[1], s));
+    PCH_CUDA(cudaEventSynchronize(ws->ev[1]));
+    const Counters& c = *ws->cnt_host;
+    if (c.error) return status_from_error(c.error);
+    if (stats) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, ws->ev[0], ws->ev[1]);
+        stats->iterations = c.iter;
+        stats->windows_created = (int64_t)c.created;
+        stats->windows_propagated = (int64_t)c.propagated;
+        stats->peak_pending = (int64_t)c.peak_pending;
+        stats->ms_total = ms;
+        stats->bytes_workspace = (int64_t)(ws->pools.bytes + ws->inst_mem.bytes + ws->fixed.bytes);
+    }
+    return PCH_OK;
+}
+
+static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_keys) {
+    SolveCfg cfg{};
+    cfg.control = opt ? opt->control : PCH_CONTROL_PLAIN;
+    cfg.loop = opt ? opt->loop : PCH_LOOP_GRAPH;
+    cfg.k = (opt && opt->k > 0) ? opt->k : default_k();
+    cfg.max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : (1LL << 31) - 1;
+    cfg.prop_threads = (opt && opt->block > 0) ? opt->block : 256;
+    cfg.prop_blocks_per_sm = 4;
+    cfg.trim = !(opt && (opt->flags & PCH_FLAG_NO_TRIM));
+    cfg.unroll = 2;
+    int bits = 1;
+    while ((1LL << bits) <= total_keys) ++bits;   // invalid key ~0u must exceed all valid keys
+    cfg.key_bits = bits;
+    cfg.mlp = nullptr;
+    (void)n_inst;
+    return cfg;
+}
+
+// Solve a set of instances.  srcs[i].inst says which instance a source seeds.
+pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* srcs, int n_src, const pch_options* opt,
+                           double* const* outs, int out_mode, pch_stats* stats) {
+    clear_error();
+    if (!meshes || n_inst <= 0 || !srcs || n_src <= 0) return set_error(PCH_ERR_INVALID_ARG, "empty solve");
+    for (int i = 0; i < n_inst; ++i)
+        if (!meshes[i]) return set_error(PCH_ERR_INVALID_ARG, "null mesh for instance %d", i);
+    for (int i = 0; i < n_src; ++i) {
+        const SrcDev& sd = srcs[i];
+        if (sd.inst < 0 || sd.inst >= n_inst) return set_error(PCH_ERR_INVALID_ARG, "bad source instance");
+        const DevMesh& dm = meshes[sd.inst]->dm;
+        if (sd.kind == 0) {
+            if (sd.vertex < 0 || sd.vertex >= dm.nv) return set_error(PCH_ERR_INVALID_ARG, "source vertex %d out of range", sd.vertex);
+        } else if (sd.kind == 1) {
+            if (sd.face < 0 || sd.face >= dm.nf) return set_error(PCH_ERR_INVALID_ARG, "source face %d out of range", sd.face);
+            double sb = sd.bary[0] + sd.bary[1] + sd.bary[2];
+            for (int k = 0; k < 3; ++k)
+                if (!(sd.bary[k] >= 0.0)) return set_error(PCH_ERR_INVALID_ARG, "negative barycentric weight");
+            if (!(std::fabs(sb - 1.0) < 1e-9)) return set_error(PCH_ERR_INVALID_ARG, "barycentric weights must sum to 1");
+        } else {
+            return set_error(PCH_ERR_INVALID_ARG, "unknown source kind %d", sd.kind);
+        }
+    }
+    cudaStream_t s = opt ? (cudaStream_t)opt->stream : (cudaStream_t)0;
+    Workspace* ws;
+    pch_status st = ensure_workspace(meshes[0], &ws);
+    if (st != PCH_OK) return st;
+    // instance layout
+    std::vector<Inst> hinst(n_inst);
+    std::vector<InstCtl> hctl(n_inst);
+    long long goff = 0, aoff = 0, kbase = 0;
+    std::vector<long long> gofs(n_inst), aofs(n_inst);
+    for (int i = 0; i < n_inst; ++i) {
+        gofs[i] = goff;
+        aofs[i] = aoff;
+        goff += meshes[i]->dm.nv;
+        aoff += meshes[i]->dm.nh;
+    }
+    st = ensure_instances(ws, n_inst, goff, aoff);
+    if (st != PCH_OK) return st;
+    SolveCfg cfg = make_cfg(opt, n_inst, aoff);
+    for (int i = 0; i < n_inst; ++i) {
+        const DevMesh& dm = meshes[i]->dm;
+        Inst& I = hinst[i];
+        I.rec = dm.rec; I.vstart = dm.vstart; I.vlist = dm.vlist; I.vphi = dm.vphi; I.vtheta = dm.vtheta;
+        I.g = ws->g_all + gofs[i];
+        I.ang = ws->ang_all + aofs[i];
+        I.stamp = ws->stamp_all + gofs[i];
+        I.fan_phi = nullptr;
+        I.nv = dm.nv; I.nh = dm.nh;
+        I.keybase = kbase;
+        kbase += dm.nh;
+        I.lbar = dm.lbar; I.ilbar = 1.0 / dm.lbar;
+        InstCtl& c = hctl[i];
+        std::memset(&c, 0, sizeof c);
+        c.kmin = ~0ull;
+        c.ref = 0.0;
+        c.k_target = cfg.k;
+        c.active = 1;
+    }
+    long long sel_want = std::max<long long>(65536, 4LL * cfg.k * std::min(n_inst, 64));
+    sel_want = std::min<long long>(sel_want, 1 << 24);
+    int pool_want = (int)std::min<long long>(std::max<long long>(2 * 6 * sel_want, 1 << 20), (1LL << 30));
+    st = ensure_pools(ws, (int)sel_want, pool_want);
+    if (st != PCH_OK) return st;
+    Work& w = ws->w;
+    w.n_inst = n_inst;
+    ws->trace_on = opt && (opt->flags & PCH_FLAG_TRACE);
+    if (ws->trace_on && !ws->trace_buf) {
+        ws->trace_cap = 1 << 18;
+        if (ws->fixed.get(&ws->trace_buf, (size_t)ws->trace_cap * (kFeatures + 2)) != cudaSuccess ||
+            ws->fixed.get(&ws->trace_rows, 1) != cudaSuccess)
+            return set_error(PCH_ERR_OOM, "trace buffer allocation failed");
+    }
+    w.trace = ws->trace_on ? ws->trace_buf : nullptr;
+    w.trace_cap = ws->trace_cap;
+    w.trace_rows = ws->trace_rows;
+    if (cfg.control == PCH_CONTROL_LEARNED) cfg.mlp = mlp_device_params();
+    // upload tables, clear state
+    PCH_CUDA(cudaMemcpyAsync(w.inst, hinst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice, s));
+    PCH_CUDA(cudaMemcpyAsync(w.ctl, hctl.data(), sizeof(InstCtl) * n_inst, cudaMemcpyHostToDevice, s));
+    PCH_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(Counters), s));
+    PCH_CUDA(cudaMemsetAsync(w.hist[0], 0, sizeof(unsigned) * kBins * n_inst, s));
+    PCH_CUDA(cudaMemsetAsync(w.hist[1], 0, sizeof(unsigned) * kBins * n_inst, s));
+    PCH_CUDA(cudaMemsetAsync(ws->ang_all, 0xff, sizeof(unsigned long long) * aoff, s));
+    PCH_CUDA(cudaMemsetAsync(ws->stamp_all, 0, sizeof(unsigned) * goff, s));
+    if (w.trace_rows) PCH_CUDA(cudaMemsetAsync(w.trace_rows, 0, sizeof(int), s));
+    k_fill_inf<<<grid_for(4), 256, 0, s>>>(ws->g_all, goff);
+    SrcDev* dsrc = nullptr;
+    PCH_CUDA(cudaMallocAsync(&dsrc, sizeof(SrcDev) * n_src, s));
+    PCH_CUDA(cudaMemcpyAsync(dsrc, srcs, sizeof(SrcDev) * n_src, cudaMemcpyHostToDevice, s));
+    k_init_sources<<<(n_src + 127) / 128, 128, 0, s>>>(w, dsrc, n_src);
+    k_init_face_sources<<<(n_src + 127) / 128, 128, 0, s>>>(w, dsrc, n_src);
+    PCH_CUDA(cudaGetLastError());
+    PCH_CUDA(cudaFreeAsync(dsrc, s));
+    st = run_solve(ws, s, cfg, stats);
+    if (st != PCH_OK) return st;
+    // results
+    for (int i = 0; i < n_inst; ++i) {
+        const DevMesh& dm = meshes[i]->dm;
+        if (out_mode == kOutDevice) {
+            k_copy_out<<<grid_for(2), 256, 0, s>>>(ws->g_all + gofs[i], outs[i], dm.nv);
+        } else if (out_mode == kOutHost) {
+            PCH_CUDA(cudaMemcpyAsync(outs[i], ws->g_all + gofs[i], sizeof(double) * dm.nv, cudaMemcpyDeviceToHost, s));
+        }
+    }
+    PCH_CUDA(cudaGetLastError());
+    if (out_mode != kOutDevice) PCH_CUDA(cudaStreamSynchronize(s));
+    return PCH_OK;
+}
+
+}  // namespace pch
+
+using namespace pch;
+
+extern "C" pch_status pch_solve(pch_mesh* m, const pch_source* src, const pch_options* opt, double* out_dist,
+                                pch_stats* stats) {
+    if (!m || !src || !out_dist) return set_error(PCH_ERR_INVALID_ARG, "null argument");
+    SrcDev sd{};
+    sd.inst = 0; sd.kind = src->kind; sd.vertex = src->vertex; sd.face = src->face;
+    for (int k = 0; k < 3; ++k) sd.bary[k] = src->bary[k];
+    double* outs[1] = {out_dist};
+    return solve_instances(&m, 1, &sd, 1, opt, outs, (opt && opt->out_on_device) ? kOutDevice : kOutHost, stats);
+}
+
+extern "C" pch_status pch_solve_multi(pch_mesh* m, const pch_source* srcs, int32_t n_sources, const pch_options* opt,
+                                      double* out_dist, pch_stats* stats) {
+    if (!m || !srcs || !out_dist || n_sources <= 0) return set_error(PCH_ERR_INVALID_ARG, "null argument");
+    std::vector<SrcDev> sd(n_sources);
+    for (int i = 0; i < n_sources; ++i) {
+        sd[i] = SrcDev{};
+        sd[i].inst = 0; sd[i].kind = srcs[i].kind; sd[i].vertex = srcs[i].vertex; sd[i].face = srcs[i].face;
+        for (int k = 0; k < 3; ++k) sd[i].bary[k] = srcs[i].bary[k];
+    }
+    double* outs[1] = {out_dist};
+    return solve_instances(&m, 1, sd.data(), n_sources, opt, outs, (opt && opt->out_on_device) ? kOutDevice : kOutHost,
+                           stats);
+}
+
+extern "C" pch_status pch_solve_batch(pch_mesh* const* meshes, const pch_source* srcs, int32_t n_instances,
+                                      const pch_options* opt, double* const* out_dists, pch_stats* stats) {
+    if (!meshes || !srcs || !out_dists || n_instances <= 0) return set_error(PCH_ERR_INVALID_ARG, "null argument");
+    std::vector<SrcDev> sd(n_instances);
+    for (int i = 0; i < n_instances; ++i) {
+        if (!out_dists[i]) return set_error(PCH_ERR_INVALID_ARG, "null output for instance %d", i);
+        sd[i] = SrcDev{};
+        sd[i].inst = i; sd[i].kind = srcs[i].kind; sd[i].vertex = srcs[i].vertex; sd[i].face = srcs[i].face;
+        for (int k = 0; k < 3; ++k) sd[i].bary[k] = srcs[i].bary[k];
+    }
+    return solve_instances(meshes, n_instances, sd.data(), n_instances, opt, out_dists,
+                           (opt && opt->out_on_device) ? kOutDevice : kOutHost, stats);
+}
+
+extern "C" pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float* chosen, int32_t* n_rows) {
+    clear_error();
+    if (!m || !n_rows) return set_error(PCH_ERR_INVALID_ARG, "null argument");
+    Workspace* ws = m->ws;
+    if (!ws || !ws->trace_buf) { *n_rows = 0; return PCH_OK; }
+    int rows = 0;
+    PCH_CUDA(cudaMemcpy(&rows, ws->trace_rows, sizeof(int), cudaMemcpyDeviceToHost));
+    rows = std::min(rows, ws->trace_cap);
+    if (max_rows < rows) rows = max_rows < 0 ? 0 : max_rows;
+    std::vector<float> buf((size_t)rows * (kFeatures + 2));
+    if (rows) PCH_CUDA(cudaMemcpy(buf.data(), ws->trace_buf, sizeof(float) * buf.size(), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < rows; ++r) {
+        if (features) std::memcpy(features + (size_t)r * kFeatures, &buf[(size_t)r * (kFeatures + 2)], sizeof(float) * kFeatures);
+        if (chosen) chosen[r] = buf[(size_t)r * (kFeatures + 2) + kFeatures];
+    }
+    *n_rows = rows;
+    return PCH_OK;
+}

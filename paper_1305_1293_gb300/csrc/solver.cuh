@@ -1,0 +1,34 @@
+#pragma once
+#include "controller.cuh"
+#include "pch_common.cuh"
+
+namespace pch {
+
+struct SrcDev {
+    int inst, kind, vertex, face;
+    double bary[3];
+};
+
+struct SolveCfg {
+    int control;
+    int loop;
+    long long k;
+    long long max_iters;
+    int prop_threads;
+    int prop_blocks_per_sm;
+    int key_bits;
+    int trim;
+    int unroll;
+    int pad;
+    const float* mlp;
+};
+
+enum { kOutHost = 0, kOutDevice = 1, kOutNone = 2 };
+
+long long default_k();
+const float* mlp_device_params();
+
+pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* srcs, int n_src,
+                           const pch_options* opt, double* const* outs, int out_mode, pch_stats* stats);
+
+}  // namespace pch

@@ -1,0 +1,228 @@
+"""Thin ctypes binding of libpch.so (include/pch.h): argument marshalling only.
+
+Every step of the geodesic computation runs in the library's CUDA kernels; this module
+converts numpy / torch arguments into pointers and status codes into exceptions.  It
+raises at import time if the in-tree library is missing (no CPU fallback exists).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpch.so")
+
+PCH_OK, PCH_ERR_INVALID_ARG, PCH_ERR_NONMANIFOLD, PCH_ERR_DEGENERATE = 0, 1, 2, 3
+PCH_ERR_OOM, PCH_ERR_CUDA, PCH_ERR_CAPACITY, PCH_ERR_TIMEOUT = 4, 5, 6, 7
+CONTROL_PLAIN, CONTROL_LEARNED, CONTROL_STRIDED = 0, 1, 2
+LOOP_GRAPH, LOOP_HOST = 0, 1
+FLAG_NO_TRIM, FLAG_FULL_FAN, FLAG_TRACE = 1, 2, 4
+
+_STATUS = {1: "INVALID_ARG", 2: "NONMANIFOLD", 3: "DEGENERATE", 4: "OOM", 5: "CUDA", 6: "CAPACITY", 7: "TIMEOUT"}
+
+
+class PchError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"PCH_ERR_{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Source(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("vertex", ctypes.c_int32), ("face", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("bary", ctypes.c_double * 3)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("control", ctypes.c_int32), ("loop", ctypes.c_int32), ("k", ctypes.c_int64),
+                ("max_iters", ctypes.c_int64), ("stream", ctypes.c_void_p), ("out_on_device", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int64), ("windows_created", ctypes.c_int64),
+                ("windows_propagated", ctypes.c_int64), ("peak_pending", ctypes.c_int64),
+                ("ms_total", ctypes.c_double), ("ms_setup", ctypes.c_double), ("bytes_workspace", ctypes.c_int64)]
+
+    def as_dict(self):
+        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() (no CPU fallback exists)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I32, I64, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+    sig = {
+        "pch_create_mesh": (I32, [P, I32, P, I32, P]),
+        "pch_mesh_info": (I32, [P, P, P, P, P]),
+        "pch_solve": (I32, [P, P, P, P, P]),
+        "pch_solve_multi": (I32, [P, P, I32, P, P, P]),
+        "pch_solve_batch": (I32, [P, P, I32, P, P, P]),
+        "pch_destroy": (None, [P]),
+        "pch_last_error": (ctypes.c_char_p, []),
+        "pch_mlp_num_features": (I32, []),
+        "pch_mlp_num_params": (I32, []),
+        "pch_mlp_set_weights": (I32, [P, I32]),
+        "pch_mlp_forward": (I32, [P, P, I32, P, P]),
+        "pch_mlp_backward": (I32, [P, P, P, I32, P, P, P]),
+        "pch_mlp_adam": (I32, [P, P, P, P, I32, ctypes.c_float, P]),
+        "pch_trace_fetch": (I32, [P, I32, P, P, P]),
+        "pch_measure_fp64_peak": (I32, [P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def _check(st: int):
+    if st != PCH_OK:
+        raise PchError(st, lib.pch_last_error().decode())
+
+
+def _ptr(a) -> int:
+    """Address of a contiguous numpy array or torch tensor (host or device)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()
+
+
+def _stream_of(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def make_options(control=CONTROL_PLAIN, loop=LOOP_GRAPH, k=0, max_iters=0, stream=None, out_on_device=False,
+                 block=0, flags=0) -> Options:
+    o = Options()
+    o.control, o.loop, o.k, o.max_iters = control, loop, k, max_iters
+    o.stream = _stream_of(stream)
+    o.out_on_device, o.block, o.flags = int(bool(out_on_device)), block, flags
+    return o
+
+
+def make_source(vertex=None, face=None, bary=None) -> Source:
+    s = Source()
+    if face is not None:
+        s.kind, s.face = 1, int(face)
+        for k in range(3):
+            s.bary[k] = float(bary[k])
+    else:
+        s.kind, s.vertex = 0, int(vertex)
+    return s
+
+
+class Mesh:
+    """A pch_mesh handle built from host arrays (vertices (V,3) f64, faces (F,3) i32)."""
+
+    def __init__(self, vertices, faces):
+        v = np.ascontiguousarray(vertices, dtype=np.float64)
+        f = np.ascontiguousarray(faces, dtype=np.int32)
+        h = ctypes.c_void_p()
+        _check(lib.pch_create_mesh(v.ctypes.data, v.shape[0], f.ctypes.data, f.shape[0], ctypes.byref(h)))
+        self.handle = h
+        self.nv, self.nf = int(v.shape[0]), int(f.shape[0])
+
+    def info(self):
+        a = [ctypes.c_int32() for _ in range(4)]
+        _check(lib.pch_mesh_info(self.handle, *[ctypes.byref(x) for x in a]))
+        return {"n_vertices": a[0].value, "n_faces": a[1].value, "n_boundary_half_edges": a[2].value,
+                "n_pseudo_vertices": a[3].value}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib.pch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def solve(mesh: Mesh, source=None, *, face=None, bary=None, out=None, stats=False, **opts):
+    """Geodesic distance from one source.  ``out``: optional torch CUDA tensor (V,) f64
+    to fill on the device; otherwise a numpy array is returned."""
+    src = make_source(source, face, bary)
+    dev = out is not None and not isinstance(out, np.ndarray)
+    o = make_options(out_on_device=dev, **opts)
+    res = out if out is not None else np.empty(mesh.nv, dtype=np.float64)
+    st = Stats()
+    _check(lib.pch_solve(mesh.handle, ctypes.byref(src), ctypes.byref(o), _ptr(res), ctypes.byref(st)))
+    return (res, st.as_dict()) if stats else res
+
+
+def solve_multi(mesh: Mesh, sources, *, out=None, stats=False, **opts):
+    srcs = (Source * len(sources))(*[make_source(s) for s in sources])
+    dev = out is not None and not isinstance(out, np.ndarray)
+    o = make_options(out_on_device=dev, **opts)
+    res = out if out is not None else np.empty(mesh.nv, dtype=np.float64)
+    st = Stats()
+    _check(lib.pch_solve_multi(mesh.handle, srcs, len(sources), ctypes.byref(o), _ptr(res), ctypes.byref(st)))
+    return (res, st.as_dict()) if stats else res
+
+
+def solve_batch(meshes, sources, *, outs=None, stats=False, **opts):
+    """Instance i: meshes[i] from vertex sources[i].  Returns a list of arrays."""
+    n = len(meshes)
+    handles = (ctypes.c_void_p * n)(*[m.handle for m in meshes])
+    srcs = (Source * n)(*[make_source(s) for s in sources])
+    dev = outs is not None and not isinstance(outs[0], np.ndarray)
+    res = outs if outs is not None else [np.empty(m.nv, dtype=np.float64) for m in meshes]
+    ptrs = (ctypes.c_void_p * n)(*[_ptr(r) for r in res])
+    o = make_options(out_on_device=dev, **opts)
+    st = Stats()
+    _check(lib.pch_solve_batch(handles, srcs, n, ctypes.byref(o), ptrs, ctypes.byref(st)))
+    return (res, st.as_dict()) if stats else res
+
+
+def mlp_num_features() -> int:
+    return lib.pch_mlp_num_features()
+
+
+def mlp_num_params() -> int:
+    return lib.pch_mlp_num_params()
+
+
+def mlp_set_weights(params: np.ndarray):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib.pch_mlp_set_weights(p.ctypes.data, p.shape[0]))
+
+
+def mlp_forward(params_dev, x_dev, y_dev, stream=None):
+    _check(lib.pch_mlp_forward(_ptr(params_dev), _ptr(x_dev), int(x_dev.shape[0]), _ptr(y_dev), _stream_of(stream)))
+
+
+def mlp_backward(params_dev, x_dev, target_dev, grad_dev, loss_dev, stream=None):
+    _check(lib.pch_mlp_backward(_ptr(params_dev), _ptr(x_dev), _ptr(target_dev), int(x_dev.shape[0]),
+                                _ptr(grad_dev), _ptr(loss_dev), _stream_of(stream)))
+
+
+def mlp_adam(params_dev, grad_dev, m_dev, v_dev, t: int, lr: float, stream=None):
+    _check(lib.pch_mlp_adam(_ptr(params_dev), _ptr(grad_dev), _ptr(m_dev), _ptr(v_dev), int(t), ctypes.c_float(lr),
+                            _stream_of(stream)))
+
+
+def trace_fetch(mesh: Mesh, max_rows: int = 1 << 18):
+    nf = mlp_num_features()
+    feats = np.empty((max_rows, nf), dtype=np.float32)
+    chosen = np.empty(max_rows, dtype=np.float32)
+    n = ctypes.c_int32()
+    _check(lib.pch_trace_fetch(mesh.handle, max_rows, feats.ctypes.data, chosen.ctypes.data, ctypes.byref(n)))
+    return feats[: n.value].copy(), chosen[: n.value].copy()
+
+
+def measure_fp64_peak() -> float:
+    t = ctypes.c_double()
+    _check(lib.pch_measure_fp64_peak(ctypes.byref(t)))
+    return t.value
