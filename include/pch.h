@@ -87,7 +87,9 @@ enum {
     PCH_FLAG_NO_TRIM = 1,     /* skip the per-edge trimming of Step 4 */
     PCH_FLAG_FULL_FAN = 2,    /* pseudo-source fans over the whole one-ring instead of the
                                  fanned area of Fig. `fig:propagation`(c) */
-    PCH_FLAG_TRACE = 4        /* record per-iteration controller features (pch_trace_fetch) */
+    PCH_FLAG_TRACE = 4,       /* record per-iteration controller features (pch_trace_fetch) */
+    PCH_FLAG_PROFILE = 8      /* host-driven loop with CUDA events around every phase
+                                 (pch_stats.ms_phase); slower, for measurement only */
 };
 
 /* Per-call statistics (the columns of Table `tab:speedup`: time, windows, peak windows). */
@@ -99,6 +101,9 @@ typedef struct {
     double ms_total;              /* device time of the solve loop (CUDA events) */
     double ms_setup;              /* device time of initialisation */
     int64_t bytes_workspace;      /* device bytes held by the solver workspace */
+    int64_t kernel_launches;      /* CUDA kernels this call launched */
+    double ms_phase[6];           /* PCH_FLAG_PROFILE: selection (tau + compaction), propagation,
+                                     fans, sort, append, loop control; else 0 */
 } pch_stats;
 
 /* Build a mesh: host arrays `vertices` (n_vertices x 3 doubles, xyz) and `faces`
@@ -162,6 +167,16 @@ pch_status pch_mlp_adam(float* params_dev, const float* grad_dev, float* m_dev, 
  * num_features floats into features (host), selected fraction into chosen (host). */
 pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float* chosen,
                            int32_t* n_rows);
+
+/* ---- autotuner (build-only) ------------------------------------------------------------
+ * Times full solves of `src` on `m` over a grid of windows-per-iteration k (powers of 4
+ * from 4096 up to the mesh's face count) and propagation block sizes (128, 256, 512),
+ * and writes the fastest into opt->k and opt->block (the other fields of *opt are kept
+ * and used for every trial).  If cache_path is not NULL the result is looked up first
+ * in, and then appended to, that text file, keyed by GPU name and mesh size, so a
+ * second call does no timing.  Errors: as pch_solve. */
+pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_options* opt, const char* cache_path,
+                        double* best_ms);
 
 /* ---- measurement helpers ---------------------------------------------------------- */
 /* Sustained FP64 FMA rate of this GPU (TFLOP/s, 2 flops per FMA) from a

@@ -67,6 +67,7 @@ struct WinSoA {
     double* px;     // pseudo-source position in the edge frame (py < 0)
     double* py;
     double* key;    // d + dist(I, [A, B]): the window's distance back to the source
+    int* src;       // mesh vertex at the pseudo-source (-1 for a point inside a face)
 };
 
 // ---- instances -------------------------------------------------------------------
@@ -74,8 +75,10 @@ struct Inst {
     const HERec* rec;
     const int* vstart;
     const int* vlist;
-    const double* vphi;
-    const double* vtheta;
+    const double* vphi;         // angular position of every half-edge around its start vertex
+    const double* vtheta;       // total angle per vertex
+    const double* hang;         // corner angle at the start vertex of every half-edge
+    const unsigned char* vflag; // bit0: boundary vertex
     unsigned long long* g;      // geod_dist[] as ordered u64 images of nonnegative doubles
     unsigned long long* ang;    // angle_split[]: packed (rounded-up distance, crossing position)
     unsigned* stamp;            // per-vertex iteration stamp (one fan request per iteration)
@@ -131,7 +134,8 @@ struct Work {
     WinSoA sel;             // selected windows
     WinSoA arena;           // children of this iteration (unsorted)
     int pool_cap, sel_cap, arena_cap, req_cap;
-    int2* req[2];           // fan requests (inst, vertex)
+    int2* req[2];           // fan candidates (inst, vertex)
+    double2* req_d[2];      // fan candidates (distance, incoming direction; NaN = all directions)
     unsigned* sort_key[2];
     int* sort_val[2];
     int* sort_hist;         // radix histograms

@@ -74,26 +74,40 @@ __device__ __forceinline__ void warp_add_ull(unsigned long long* c, int x) {
     if ((threadIdx.x & 31) == 0 && t) atomicAdd(c, (unsigned long long)t);
 }
 
-// Distance event (Algorithm 2, Algorithm 4): min into geod_dist; a pseudo-source vertex
-// whose distance dropped gets one fan request per iteration.
-__device__ __forceinline__ void vertex_event(const Inst& I, int inst, unsigned vf, double D, double& gcache,
-                                             unsigned stamp_val, int2* req, int* n_req, int req_cap, int* err) {
-    if (!(D < gcache)) return;
+// Distance event (Algorithm 2, Algorithm 4): min into geod_dist.  Returns true when the
+// event lowered the distance of a pseudo-source vertex: the caller then files a fan
+// candidate carrying the event's incoming direction.
+__device__ __forceinline__ bool vertex_event(const Inst& I, unsigned vf, double D, double& gcache) {
+    if (!(D < gcache)) return false;
     unsigned v = vf & ~kPseudoBit;
     unsigned long long nb = dbits(D);
     unsigned long long old = atomicMin(I.g + v, nb);
     if (nb < old) {
         gcache = D;
-        if (vf & kPseudoBit) {
-            if (atomicExch(I.stamp + v, stamp_val) != stamp_val) {
-                int slot = atomicAdd(n_req, 1);
-                if (slot < req_cap) req[slot] = make_int2(inst, (int)v);
-                else atomicOr(err, kErrReqFull);
-            }
-        }
-    } else {
-        gcache = bitsd(old);
+        return (vf & kPseudoBit) != 0;
     }
+    gcache = bitsd(old);
+    return false;
+}
+
+__device__ __forceinline__ void push_fan(int2* req, double2* req_d, int* n, int cap, int* err, int inst, unsigned v,
+                                         double D, double phi) {
+    int slot = atomicAdd(n, 1);
+    if (slot < cap) {
+        req[slot] = make_int2(inst, (int)v);
+        req_d[slot] = make_double2(D, phi);
+    } else {
+        atomicOr(err, kErrReqFull);
+    }
+}
+
+// Angular coordinate of a direction at vertex v: interior vertices wrap modulo the total
+// angle, boundary vertices clamp to [0, total angle].
+__device__ __forceinline__ double wrap_angle(const Inst& I, unsigned v, double a) {
+    double T = I.vtheta[v];
+    if (I.vflag[v] & 1) return fmin(fmax(a, 0.0), T);
+    a = fmod(a, T);
+    return a < 0.0 ? a + T : a;
 }
 
 __device__ __forceinline__ int hist_bin(double key, double ref, double ilbar) {
@@ -148,12 +162,22 @@ __device__ __forceinline__ void pool_stat(const Work& w, const PoolStats& ps, in
 }
 
 __device__ __forceinline__ void load_win(const WinSoA& s, int i, int& he, int& inst, double& d, double& A, double& B,
-                                         double& px, double& py, double& key) {
+                                         double& px, double& py, double& key, int& src) {
     he = s.he[i]; inst = s.inst[i]; d = s.d[i]; A = s.A[i]; B = s.B[i]; px = s.px[i]; py = s.py[i]; key = s.key[i];
+    src = s.src[i];
 }
 __device__ __forceinline__ void store_win(const WinSoA& s, int i, int he, int inst, double d, double A, double B,
-                                          double px, double py, double key) {
+                                          double px, double py, double key, int src) {
     s.he[i] = he; s.inst[i] = inst; s.d[i] = d; s.A[i] = A; s.B[i] = B; s.px[i] = px; s.py[i] = py; s.key[i] = key;
+    s.src[i] = src;
+}
+
+// A window whose pseudo-source vertex has since been reached by a shorter path is
+// useless: the same straight segment from that vertex, after the shorter path, is a
+// real path of smaller length (build-side filter; the paper's filters are in Fig.
+// `fig:filter`).
+__device__ __forceinline__ bool stale_source(const Inst& I, int src, double d) {
+    return src >= 0 && dominated(d, bitsd(__ldcg(I.g + src)));
 }
 
 // ====================================================================== init
@@ -173,11 +197,8 @@ __global__ void k_init_sources(Work w, const SrcDev* __restrict__ srcs, int n_sr
         const Inst& I = w.inst[s.inst];
         if (s.kind == 0) {
             I.g[s.vertex] = 0ull;
-            if (atomicExch(I.stamp + s.vertex, 1u) != 1u) {
-                int slot = atomicAdd(&cnt->n_req, 1);
-                if (slot < w.req_cap) w.req[0][slot] = make_int2(s.inst, s.vertex);
-                else atomicOr(&cnt->error, kErrReqFull);
-            }
+            // the source's fan covers every direction
+            push_fan(w.req[0], w.req_d[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, (unsigned)s.vertex, 0.0, NAN);
         }
     }
 }
@@ -198,14 +219,19 @@ __global__ void k_init_face_sources(Work w, const SrcDev* __restrict__ srcs, int
             double x = b1 * R.L + b2 * R.xc, y = b2 * R.yc;        // point in h's frame
             double dstart = sqrt(x * x + y * y);
             double gc = ldg_dist(I.g, R.v0 & ~kPseudoBit);
-            vertex_event(I, s.inst, R.v0, dstart, gc, 1u, w.req[0], &cnt->n_req, w.req_cap, &cnt->error);
+            if (vertex_event(I, R.v0, dstart, gc)) {
+                // incoming direction: from the corner towards the point, inside face(h)
+                double phi = wrap_angle(I, R.v0 & ~kPseudoBit, I.vphi[h] + atan2(y, x));
+                push_fan(w.req[0], w.req_d[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, R.v0 & ~kPseudoBit,
+                         dstart, phi);
+            }
             if (R.twin < 0) continue;
             // window on twin(h) = (v1 -> v0): point at (L - x, -y), interval [0, L]
             double px = R.L - x, py = -y;
             double key = px < 0 ? sqrt(px * px + py * py)
                                 : (px > R.L ? sqrt((px - R.L) * (px - R.L) + py * py) : -py);
             int slot = atomicAdd(&cnt->n_child, 1);
-            if (slot < w.arena_cap) store_win(w.arena, slot, R.twin, s.inst, 0.0, 0.0, R.L, px, py, key);
+            if (slot < w.arena_cap) store_win(w.arena, slot, R.twin, s.inst, 0.0, 0.0, R.L, px, py, key, -1);
         }
     }
 }
@@ -295,16 +321,19 @@ __global__ void __launch_bounds__(256) k_compact(Work w) {
     for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         int i = base + threadIdx.x;
         bool valid = i < n;
-        int he = 0, inst = 0;
+        int he = 0, inst = 0, src = -1;
         double d = 0, A = 0, B = 0, px = 0, py = 0, key = 0;
-        if (valid) load_win(cur, i, he, inst, d, A, B, px, py, key);
+        if (valid) {
+            load_win(cur, i, he, inst, d, A, B, px, py, key, src);
+            if (stale_source(w.inst[inst], src, d)) valid = false;   // dropped from the pool
+        }
         bool sel = valid && key <= w.ctl[inst].tau;
         int slot = warp_reserve(&cnt->n_sel, sel ? 1 : 0);
         if (sel && slot >= w.sel_cap) sel = false;   // work list full: stays pending
-        if (sel) store_win(w.sel, slot, he, inst, d, A, B, px, py, key);
+        if (sel) store_win(w.sel, slot, he, inst, d, A, B, px, py, key, src);
         bool rest = valid && !sel;
         int rslot = warp_reserve(&cnt->n_rest, rest ? 1 : 0);
-        if (rest) store_win(nxt, rslot, he, inst, d, A, B, px, py, key);
+        if (rest) store_win(nxt, rslot, he, inst, d, A, B, px, py, key, src);
         pool_stat(w, ps, inst, key, rest);
     }
     if (ps.sh_hist) {
@@ -347,17 +376,18 @@ __global__ void __launch_bounds__(256) k_propagate(Work w) {
     const int it = cnt->iter;
     const int n = min(cnt->n_sel, w.sel_cap);
     int2* req = w.req[it & 1];
-    const unsigned stamp_val = (unsigned)it + 1u;
+    double2* req_d = w.req_d[it & 1];
     for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const int i = base + threadIdx.x;
         ChildOut c[2];
-        int nc = 0, inst = 0;
+        int nc = 0, inst = 0, src = -1;
         double d = 0.0;
         bool prop = false;
         if (i < n) {
             const int h = w.sel.he[i];
             inst = w.sel.inst[i];
             d = w.sel.d[i];
+            src = w.sel.src[i];
             const double A = w.sel.A[i], B = w.sel.B[i], px = w.sel.px[i], py = w.sel.py[i];
             const Inst& I = w.inst[inst];
             const HERec R = I.rec[h];
@@ -370,18 +400,27 @@ __global__ void __launch_bounds__(256) k_propagate(Work w) {
             const double IA = sqrt(ax * ax + py2), IB = sqrt(bx * bx + py2);
             // Xin-Wang endpoint tests against the current distances: the window is
             // useless if the path via v0 beats it at B, or the path via v1 at A.
-            if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)))) {
+            if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)) || stale_source(I, src, d))) {
                 prop = true;
                 const double tol = kEpsSnap * L;
                 // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
                 if (A <= tol) {
                     double D0 = d + (A == 0.0 ? IA : sqrt(px * px + py2));
-                    vertex_event(I, inst, R.v0, D0, g0, stamp_val, req, &cnt->n_req, w.req_cap, &cnt->error);
+                    if (vertex_event(I, R.v0, D0, g0)) {
+                        // the ray arrives at v0 through the twin face: direction to I
+                        const unsigned v = R.v0 & ~kPseudoBit;
+                        push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D0,
+                                 wrap_angle(I, v, I.vphi[h] + atan2(py, px)));
+                    }
                 }
                 if (B >= L - tol) {
                     double q = L - px;
                     double D1 = d + (B == L ? IB : sqrt(q * q + py2));
-                    vertex_event(I, inst, R.v1, D1, g1, stamp_val, req, &cnt->n_req, w.req_cap, &cnt->error);
+                    if (vertex_event(I, R.v1, D1, g1)) {
+                        const unsigned v = R.v1 & ~kPseudoBit;
+                        push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D1,
+                                 wrap_angle(I, v, I.vphi[R.twin] + atan2(py, -q) + 3.14159265358979323846));
+                    }
                 }
                 // occupancy of v2: the ray I -> v2 crosses e at xs
                 const double xc = R.xc, yc = R.yc;
@@ -409,7 +448,16 @@ __global__ void __launch_bounds__(256) k_propagate(Work w) {
                         right = xs > (q + 1.0) * sc + tol;
                         if (!left && !right) left = right = true;
                     }
-                    vertex_event(I, inst, R.v2, D2, g2, stamp_val, req, &cnt->n_req, w.req_cap, &cnt->error);
+                    if (vertex_event(I, R.v2, D2, g2)) {
+                        // the ray arrives at v2 inside face(h): angle from v2->v0 towards I
+                        const unsigned v = R.v2 & ~kPseudoBit;
+                        const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
+                        double da = atan2(py - yc, px - xc) - atan2(-yc, -xc);
+                        if (da < 0.0) da += 2.0 * 3.14159265358979323846;
+                        da = fmin(da, I.hang[hp]);
+                        push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D2,
+                                 wrap_angle(I, v, I.vphi[hp] + da));
+                    }
                     if (B - xcl <= kEpsTiny * L) right = false;
                     if (xcl - A <= kEpsTiny * L) left = false;
                 } else {
@@ -471,63 +519,143 @@ __global__ void __launch_bounds__(256) k_propagate(Work w) {
         int slot = warp_reserve(&cnt->n_child, nc);
         for (int j = 0; j < nc; ++j) {
             int s = slot + j;
-            if (s < w.arena_cap) store_win(w.arena, s, c[j].he, inst, d, c[j].A, c[j].B, c[j].px, c[j].py, c[j].key);
+            if (s < w.arena_cap) store_win(w.arena, s, c[j].he, inst, d, c[j].A, c[j].B, c[j].px, c[j].py, c[j].key, src);
             else atomicOr(&cnt->error, kErrPoolFull);
         }
         warp_add_ull(&cnt->propagated, prop ? 1 : 0);
     }
 }
 
-// Pseudo-source fans (Fig. `fig:propagation`(c)): for every vertex whose distance dropped
-// this iteration, one window on each edge of its one-ring opposite it, with I = the
-// vertex and d = its distance.  Boundary edges get their endpoint events instead.
-__global__ void k_fan(Work w) {
+// Pseudo-source fans (Fig. `fig:propagation`(c)).  For each fan candidate whose distance
+// is still the vertex's distance (one per vertex per iteration): windows with I = the
+// vertex and d = its distance on the edges opposite it, restricted to the fanned area:
+// the directions at least pi away from the incoming ray on both sides (a wedge of width
+// total angle - 2 pi at an interior saddle; at a boundary vertex the directions that
+// wrap around it).  Boundary edges get their endpoint events instead of a window.
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kWedgeEps = 1e-9;    // the wedge is widened by this angle on each side
+
+struct Wedges {
+    double lo[2], hi[2];
+    int n;
+    int shifts;     // interior vertices: test the wedge shifted by -T, 0, +T
+};
+
+__device__ __forceinline__ Wedges make_wedges(bool boundary, double T, double phi, bool full) {
+    Wedges W;
+    W.n = 0;
+    W.shifts = 0;
+    if (full || !(phi == phi)) {
+        W.lo[0] = -1e300; W.hi[0] = 1e300; W.n = 1;
+        return W;
+    }
+    if (boundary) {
+        if (phi - kPi > -kWedgeEps) { W.lo[W.n] = -1.0; W.hi[W.n] = phi - kPi + kWedgeEps; ++W.n; }
+        if (phi + kPi < T + kWedgeEps) { W.lo[W.n] = phi + kPi - kWedgeEps; W.hi[W.n] = T + 1.0; ++W.n; }
+    } else if (T - 2.0 * kPi > -kWedgeEps) {
+        W.lo[0] = phi + kPi - kWedgeEps; W.hi[0] = phi + T - kPi + kWedgeEps; W.n = 1; W.shifts = 1;
+    }
+    return W;
+}
+
+// Part [b0, b1] (angles from the face's first edge at the vertex) of corner [c0, c0 + c]
+// covered by the wedges; false if none.
+__device__ __forceinline__ bool wedge_part(const Wedges& W, double T, double c0, double c, double& b0, double& b1) {
+    for (int wi = 0; wi < W.n; ++wi)
+        for (int j = -W.shifts; j <= W.shifts; ++j) {
+            double a = fmax(W.lo[wi] + j * T, c0), b = fmin(W.hi[wi] + j * T, c0 + c);
+            if (b >= a) {
+                b0 = a - c0;
+                b1 = b - c0;
+                return true;
+            }
+        }
+    return false;
+}
+
+// Where the ray from the apex v of o's face, at angle beta from v->start(o), meets o:
+// distance from start(o) along o (o's frame: start at 0, v at (xc, yc)).
+__device__ __forceinline__ double fan_hit(const HERec& Ro, double beta) {
+    double sb, cb;
+    sincos(beta, &sb, &cb);
+    const double iva = 1.0 / Ro.L2;
+    const double ux = -Ro.xc * iva, uy = -Ro.yc * iva;
+    const double dx = ux * cb - uy * sb, dy = ux * sb + uy * cb;
+    double s = Ro.xc - Ro.yc * dx / dy;
+    return fmin(fmax(s, 0.0), Ro.L);
+}
+
+__global__ void k_fan(Work w, int full_fan) {
     Counters* cnt = w.cnt;
     if (cnt->halt) return;
     const int it = cnt->iter;
     const int nreq = min(cnt->n_req, w.req_cap);
     const int2* req = w.req[it & 1];
+    const double2* req_d = w.req_d[it & 1];
     int2* req_nx = w.req[(it + 1) & 1];
-    const unsigned stamp_nx = (unsigned)it + 2u;
+    double2* req_d_nx = w.req_d[(it + 1) & 1];
+    const unsigned stamp_fan = (unsigned)it + 1u;
     for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreq; r += gridDim.x * blockDim.x) {
         const int inst = req[r].x;
         const unsigned v = (unsigned)req[r].y;
+        const double D = req_d[r].x, phi = req_d[r].y;
         const Inst& I = w.inst[inst];
-        const double D = ldg_dist(I.g, v);
+        if (dbits(D) != __ldcg(I.g + v)) continue;                  // superseded by a shorter event
+        if (atomicExch(I.stamp + v, stamp_fan) == stamp_fan) continue;   // one fan per vertex per iteration
         const int s = I.vstart[v], e = I.vstart[v + 1];
-        const int deg = e - s;
-        const int base = atomicAdd(&cnt->n_child, deg);
-        if (base + deg > w.arena_cap) {
-            // no room this iteration: mark the reserved slots empty, retry next iteration
-            for (int j = base; j < min(base + deg, w.arena_cap); ++j) w.arena.he[j] = -1;
-            atomicExch(I.stamp + v, stamp_nx);
-            int slot = atomicAdd(&cnt->n_req_next, 1);
-            if (slot < w.req_cap) req_nx[slot] = make_int2(inst, (int)v);
-            else atomicOr(&cnt->error, kErrReqFull);
+        const double T = I.vtheta[v];
+        const Wedges W = make_wedges(I.vflag[v] & 1, T, phi, full_fan != 0);
+        if (W.n == 0) continue;
+        // pass 1: windows this fan creates
+        int count = 0;
+        for (int j = s; j < e; ++j) {
+            const int hv = I.vlist[j];
+            double b0, b1;
+            if (wedge_part(W, T, I.vphi[hv], I.hang[hv], b0, b1) && I.rec[he_next(hv)].twin >= 0) ++count;
+        }
+        const int base = atomicAdd(&cnt->n_child, count);
+        if (base + count > w.arena_cap) {
+            // no room this iteration: mark the reserved slots empty and retry next iteration
+            for (int j = base; j < min(base + count, w.arena_cap); ++j) w.arena.he[j] = -1;
+            atomicExch(I.stamp + v, 0u);
+            push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, v, D, phi);
             continue;
         }
-        for (int j = 0; j < deg; ++j) {
-            const int hv = I.vlist[s + j];
+        int slot = base;
+        for (int j = s; j < e; ++j) {
+            const int hv = I.vlist[j];
+            double b0, b1;
+            const double c = I.hang[hv];
+            if (!wedge_part(W, T, I.vphi[hv], c, b0, b1)) continue;
             const int o = he_next(hv);                 // edge (a -> b) opposite v
             const HERec Ro = I.rec[o];
-            const double va = Ro.L2, vb = Ro.L1;       // |v a|, |v b|
-            double ga = ldg_dist(I.g, Ro.v0 & ~kPseudoBit), gb = ldg_dist(I.g, Ro.v1 & ~kPseudoBit);
-            const int slot = base + j;
-            if (Ro.twin < 0) {
-                vertex_event(I, inst, Ro.v0, D + va, ga, stamp_nx, req_nx, &cnt->n_req_next, w.req_cap, &cnt->error);
-                vertex_event(I, inst, Ro.v1, D + vb, gb, stamp_nx, req_nx, &cnt->n_req_next, w.req_cap, &cnt->error);
-                w.arena.he[slot] = -1;
-                continue;
-            }
             const double Lo = Ro.L;
-            // window on twin(o) = (b -> a): I = v at (Lo - xc, -yc), interval [0, Lo]
-            if (dominated(D + va, gb + Lo) || dominated(D + vb, ga + Lo)) {
-                w.arena.he[slot] = -1;
+            const double s0 = b0 <= 1e-12 ? 0.0 : fan_hit(Ro, b0);
+            const double s1 = b1 >= c - 1e-12 ? Lo : fan_hit(Ro, b1);
+            if (Ro.twin < 0) {
+                // boundary edge: endpoint events for the covered endpoints
+                const unsigned a = Ro.v0 & ~kPseudoBit, b = Ro.v1 & ~kPseudoBit;
+                double ga = ldg_dist(I.g, a), gb = ldg_dist(I.g, b);
+                if (s0 <= 0.0 && vertex_event(I, Ro.v0, D + Ro.L2, ga))
+                    push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, a, D + Ro.L2,
+                             wrap_angle(I, a, I.vphi[o] + I.hang[o]));
+                if (s1 >= Lo && vertex_event(I, Ro.v1, D + Ro.L1, gb))
+                    push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, b, D + Ro.L1,
+                             wrap_angle(I, b, I.vphi[he_next(o)]));
                 continue;
             }
+            // window on twin(o) = (b -> a): I = v at (Lo - xc, -yc), interval [Lo - s1, Lo - s0]
+            const double A = Lo - s1, B = Lo - s0;
+            const int sl = slot++;
             const double px = Lo - Ro.xc, py = -Ro.yc;
-            const double key = D + (px < 0.0 ? vb : (px > Lo ? va : Ro.yc));
-            store_win(w.arena, slot, Ro.twin, inst, D, 0.0, Lo, px, py, key);
+            const double IA = sqrt((A - px) * (A - px) + py * py), IB = sqrt((B - px) * (B - px) + py * py);
+            const double ga = ldg_dist(I.g, Ro.v0 & ~kPseudoBit), gb = ldg_dist(I.g, Ro.v1 & ~kPseudoBit);
+            if (!(B - A > kEpsTiny * Lo) || dominated(D + IB, gb + B) || dominated(D + IA, ga + (Lo - A))) {
+                w.arena.he[sl] = -1;
+                continue;
+            }
+            const double key = D + (px < A ? IA : (px > B ? IB : -py));
+            store_win(w.arena, sl, Ro.twin, inst, D, A, B, px, py, key, (int)v);
         }
     }
 }
@@ -552,17 +680,17 @@ __global__ void __launch_bounds__(256) k_append(Work w, const unsigned* __restri
         const int i = base + threadIdx.x;
         unsigned k = i < n ? keys[i] : ~0u;
         bool keep = k != ~0u;
-        int he = 0, inst = 0;
+        int he = 0, inst = 0, src = -1;
         double d = 0, A = 0, B = 0, px = 0, py = 0, key = 0;
         int trimmed = 0;
         if (keep) {
-            load_win(w.arena, vals[i], he, inst, d, A, B, px, py, key);
+            load_win(w.arena, vals[i], he, inst, d, A, B, px, py, key, src);
             const Inst& I = w.inst[inst];
             const HERec R = I.rec[he];
             // re-filter against the distances after this iteration's events (the window
             // is nowhere closer than `key`)
             double g0 = ldg_dist(I.g, R.v0 & ~kPseudoBit), g1 = ldg_dist(I.g, R.v1 & ~kPseudoBit);
-            if (dominated(key, g0 + B) || dominated(key, g1 + (R.L - A))) keep = false;
+            if (dominated(key, g0 + B) || dominated(key, g1 + (R.L - A)) || stale_source(I, src, d)) keep = false;
             // per-edge trimming: a window on the same edge that covers [A, B] and is
             // everywhere shorter than this window's nearest point makes it useless
             if (keep && trim) {
@@ -584,7 +712,7 @@ __global__ void __launch_bounds__(256) k_append(Work w, const unsigned* __restri
         int slot = warp_reserve(&cnt->n_app, keep ? 1 : 0);
         if (keep) {
             int pos = n_rest + slot;
-            if (pos < w.pool_cap) store_win(nxt, pos, he, inst, d, A, B, px, py, key);
+            if (pos < w.pool_cap) store_win(nxt, pos, he, inst, d, A, B, px, py, key, src);
             else atomicOr(&cnt->error, kErrPoolFull);
         }
         pool_stat(w, ps, inst, key, keep);
@@ -706,7 +834,8 @@ static cudaError_t alloc_soa(Alloc& a, WinSoA& s, int cap) {
     if ((e = a.get(&s.B, cap))) return e;
     if ((e = a.get(&s.px, cap))) return e;
     if ((e = a.get(&s.py, cap))) return e;
-    return a.get(&s.key, cap);
+    if ((e = a.get(&s.key, cap))) return e;
+    return a.get(&s.src, cap);
 }
 
 static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap) {
@@ -729,6 +858,8 @@ static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap) {
     if (!e) e = alloc_soa(fresh, nw.arena, arena_cap);
     if (!e) e = fresh.get(&nw.req[0], req_cap);
     if (!e) e = fresh.get(&nw.req[1], req_cap);
+    if (!e) e = fresh.get(&nw.req_d[0], req_cap);
+    if (!e) e = fresh.get(&nw.req_d[1], req_cap);
     if (!e) e = fresh.get(&nw.sort_key[0], arena_cap);
     if (!e) e = fresh.get(&nw.sort_key[1], arena_cap);
     if (!e) e = fresh.get(&nw.sort_val[0], arena_cap);
@@ -751,7 +882,9 @@ static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap) {
             cudaMemcpy(nw.pool[p].px, w.pool[p].px, n * 8, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.pool[p].py, w.pool[p].py, n * 8, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.pool[p].key, w.pool[p].key, n * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].src, w.pool[p].src, n * 4, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.req[p], w.req[p], sizeof(int2) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.req_d[p], w.req_d[p], sizeof(double2) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
         }
         e = cudaDeviceSynchronize();
         if (e) { fresh.release(); return set_error(PCH_ERR_CUDA, "pool growth copy: %s", cudaGetErrorString(e)); }
@@ -822,21 +955,35 @@ static pch_status ensure_instances(Workspace* ws, int n_inst, long long g_total,
 
 static int grid_for(int blocks_per_sm) { return sm_count() * blocks_per_sm; }
 
-// Launch one iteration (all phases).  Returns a CUDA error if a launch failed.
+// Kernels one iteration launches (for pch_stats.kernel_launches).
+static int kernels_per_iteration(const SolveCfg& cfg) {
+    int passes = (cfg.key_bits + kRsDigitBits - 1) / kRsDigitBits;
+    return 7 + 3 * (passes < 1 ? 1 : passes);
+}
+
+// Launch one iteration (all phases).  With `ev` (7 events) the phase boundaries are
+// recorded for PCH_FLAG_PROFILE.  Returns a CUDA error if a launch failed.
 static cudaError_t launch_iteration(Workspace* ws, cudaStream_t s, const SolveCfg& cfg, cudaGraphConditionalHandle h,
-                                    int use_cond) {
+                                    int use_cond, cudaEvent_t* ev = nullptr) {
     Work& w = ws->w;
     const int tpb = 256;
+    if (ev) cudaEventRecord(ev[0], s);
     k_tau<<<std::min(w.n_inst, 1024), 256, 0, s>>>(w, cfg.control, cfg.mlp);
     k_compact<<<grid_for(4), tpb, 0, s>>>(w);
+    if (ev) cudaEventRecord(ev[1], s);
     k_propagate<<<grid_for(cfg.prop_blocks_per_sm), cfg.prop_threads, 0, s>>>(w);
-    k_fan<<<grid_for(2), 128, 0, s>>>(w);
+    if (ev) cudaEventRecord(ev[2], s);
+    k_fan<<<grid_for(2), 128, 0, s>>>(w, cfg.full_fan);
+    if (ev) cudaEventRecord(ev[3], s);
     unsigned* kb[2] = {w.sort_key[0], w.sort_key[1]};
     int* vb[2] = {w.sort_val[0], w.sort_val[1]};
     int par = launch_sort_children(w.arena, w.inst, &w.cnt->n_child, w.arena_cap, cfg.key_bits, kb, vb, w.sort_hist,
                                    w.sort_blocks, s);
+    if (ev) cudaEventRecord(ev[4], s);
     k_append<<<grid_for(4), tpb, 0, s>>>(w, kb[par], vb[par], cfg.trim);
+    if (ev) cudaEventRecord(ev[5], s);
     k_finish<<<1, 1, 0, s>>>(w, h, use_cond, cfg.max_iters);
+    if (ev) cudaEventRecord(ev[6], s);
     return cudaGetLastError();
 }
 
@@ -882,17 +1029,33 @@ static pch_status status_from_error(int err) {
     return set_error(PCH_ERR_CUDA, "solver error flags %d", err);
 }
 
-// Common driver: instances already described by `specs` and `srcs_dev`.
+// Common driver: runs the iterations of an initialised solve.
 static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_in, pch_stats* stats) {
     SolveCfg cfg = cfg_in;
     Work& w = ws->w;
-    // iterations
+    long long launches = 0;
+    double phase_ms[6] = {0, 0, 0, 0, 0, 0};
     PCH_CUDA(cudaEventRecord(ws->ev[0], s));
-    if (cfg.loop == PCH_LOOP_HOST) {
+    if (cfg.loop == PCH_LOOP_HOST || cfg.profile) {
+        cudaEvent_t pev[7];
+        if (cfg.profile)
+            for (auto& e : pev) PCH_CUDA(cudaEventCreate(&e));
         for (long long it = 0;; ++it) {
-            PCH_CUDA(launch_iteration(ws, s, cfg, 0, 0));
+            cudaError_t le = launch_iteration(ws, s, cfg, 0, 0, cfg.profile ? pev : nullptr);
+            if (le) {
+                if (cfg.profile) for (auto& e : pev) cudaEventDestroy(e);
+                PCH_CUDA(le);
+            }
+            launches += kernels_per_iteration(cfg);
             PCH_CUDA(cudaMemcpyAsync(ws->cnt_host, w.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
             PCH_CUDA(cudaStreamSynchronize(s));
+            if (cfg.profile) {
+                for (int p = 0; p < 6; ++p) {
+                    float ms = 0.f;
+                    cudaEventElapsedTime(&ms, pev[p], pev[p + 1]);
+                    phase_ms[p] += ms;
+                }
+            }
             const Counters& c = *ws->cnt_host;
             if (c.error || c.done) break;
             if (c.n_pending + w.arena_cap > w.pool_cap) {
@@ -901,6 +1064,7 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
                 PCH_CUDA(cudaMemsetAsync(&w.cnt->halt, 0, sizeof(int), s));
             }
         }
+        if (cfg.profile) for (auto& e : pev) cudaEventDestroy(e);
     } else {
         while (true) {
             GraphKey key{};
@@ -915,6 +1079,7 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
             PCH_CUDA(cudaMemcpyAsync(ws->cnt_host, w.cnt, sizeof(Counters), cudaMemcpyDeviceToHost, s));
             PCH_CUDA(cudaStreamSynchronize(s));
             const Counters& c = *ws->cnt_host;
+            // the WHILE body ran ceil(iterations / unroll) times
             if (c.error || c.done) break;
             if (c.n_pending + w.arena_cap > w.pool_cap) {
                 pch_status st = ensure_pools(ws, ws->sel_cap, 2 * ws->pool_cap);
@@ -923,6 +1088,8 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
                 continue;
             }
         }
+        const long long it = ws->cnt_host->iter;
+        launches += ((it + cfg.unroll - 1) / cfg.unroll) * cfg.unroll * kernels_per_iteration(cfg);
     }
     PCH_CUDA(cudaEventRecord(ws->ev[1], s));
     PCH_CUDA(cudaEventSynchronize(ws->ev[1]));
@@ -937,6 +1104,8 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         stats->peak_pending = (int64_t)c.peak_pending;
         stats->ms_total = ms;
         stats->bytes_workspace = (int64_t)(ws->pools.bytes + ws->inst_mem.bytes + ws->fixed.bytes);
+        stats->kernel_launches += launches;
+        for (int p = 0; p < 6; ++p) stats->ms_phase[p] = phase_ms[p];
     }
     return PCH_OK;
 }
@@ -950,6 +1119,8 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     cfg.prop_threads = (opt && opt->block > 0) ? opt->block : 256;
     cfg.prop_blocks_per_sm = 4;
     cfg.trim = !(opt && (opt->flags & PCH_FLAG_NO_TRIM));
+    cfg.full_fan = (opt && (opt->flags & PCH_FLAG_FULL_FAN)) ? 1 : 0;
+    cfg.profile = (opt && (opt->flags & PCH_FLAG_PROFILE)) ? 1 : 0;
     cfg.unroll = 2;
     int bits = 1;
     while ((1LL << bits) <= total_keys) ++bits;   // invalid key ~0u must exceed all valid keys
@@ -1004,6 +1175,7 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
         const DevMesh& dm = meshes[i]->dm;
         Inst& I = hinst[i];
         I.rec = dm.rec; I.vstart = dm.vstart; I.vlist = dm.vlist; I.vphi = dm.vphi; I.vtheta = dm.vtheta;
+        I.hang = dm.hang; I.vflag = dm.vflag;
         I.g = ws->g_all + gofs[i];
         I.ang = ws->ang_all + aofs[i];
         I.stamp = ws->stamp_all + gofs[i];
@@ -1046,6 +1218,7 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
     PCH_CUDA(cudaMemsetAsync(ws->ang_all, 0xff, sizeof(unsigned long long) * aoff, s));
     PCH_CUDA(cudaMemsetAsync(ws->stamp_all, 0, sizeof(unsigned) * goff, s));
     if (w.trace_rows) PCH_CUDA(cudaMemsetAsync(w.trace_rows, 0, sizeof(int), s));
+    if (stats) std::memset(stats, 0, sizeof(pch_stats));
     k_fill_inf<<<grid_for(4), 256, 0, s>>>(ws->g_all, goff);
     SrcDev* dsrc = nullptr;
     PCH_CUDA(cudaMallocAsync(&dsrc, sizeof(SrcDev) * n_src, s));
@@ -1054,13 +1227,16 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
     k_init_face_sources<<<(n_src + 127) / 128, 128, 0, s>>>(w, dsrc, n_src);
     PCH_CUDA(cudaGetLastError());
     PCH_CUDA(cudaFreeAsync(dsrc, s));
+    if (stats) stats->kernel_launches = 3;
     st = run_solve(ws, s, cfg, stats);
     if (st != PCH_OK) return st;
     // results
     for (int i = 0; i < n_inst; ++i) {
         const DevMesh& dm = meshes[i]->dm;
+        if (out_mode == kOutNone) continue;
         if (out_mode == kOutDevice) {
             k_copy_out<<<grid_for(2), 256, 0, s>>>(ws->g_all + gofs[i], outs[i], dm.nv);
+            if (stats) stats->kernel_launches += 1;
         } else if (out_mode == kOutHost) {
             PCH_CUDA(cudaMemcpyAsync(outs[i], ws->g_all + gofs[i], sizeof(double) * dm.nv, cudaMemcpyDeviceToHost, s));
         }
@@ -1128,5 +1304,75 @@ extern "C" pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* feat
         if (chosen) chosen[r] = buf[(size_t)r * (kFeatures + 2) + kFeatures];
     }
     *n_rows = rows;
+    return PCH_OK;
+}
+
+// ---------------------------------------------------------------- autotuner
+#include <fstream>
+#include <sstream>
+#include <string>
+
+extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_options* opt, const char* cache_path,
+                                   double* best_ms) {
+    clear_error();
+    if (!m || !src || !opt) return set_error(PCH_ERR_INVALID_ARG, "null argument");
+    cudaDeviceProp prop;
+    int dev = 0;
+    PCH_CUDA(cudaGetDevice(&dev));
+    PCH_CUDA(cudaGetDeviceProperties(&prop, dev));
+    std::string name(prop.name);
+    for (auto& ch : name) if (ch == ' ' || ch == '|') ch = '_';
+    std::ostringstream keyss;
+    keyss << name << "|nv=" << m->dm.nv << "|nf=" << m->dm.nf << "|control=" << opt->control;
+    const std::string key = keyss.str();
+    if (cache_path) {
+        std::ifstream in(cache_path);
+        std::string line;
+        while (std::getline(in, line)) {
+            std::istringstream ls(line);
+            std::string k2;
+            long long kk;
+            int bb;
+            double ms;
+            if (ls >> k2 >> kk >> bb >> ms && k2 == key) {
+                opt->k = kk;
+                opt->block = bb;
+                if (best_ms) *best_ms = ms;
+                return PCH_OK;
+            }
+        }
+    }
+    SrcDev sd{};
+    sd.kind = src->kind; sd.vertex = src->vertex; sd.face = src->face;
+    for (int q = 0; q < 3; ++q) sd.bary[q] = src->bary[q];
+    pch_options trial = *opt;
+    trial.out_on_device = 0;
+    double best = 1e300;
+    long long best_k = 0;
+    int best_b = 0;
+    std::vector<long long> ks;
+    for (long long k = 4096; k <= std::max<long long>(4096, 4LL * m->dm.nf); k *= 4) ks.push_back(k);
+    const int blocks[3] = {128, 256, 512};
+    for (long long k : ks) {
+        for (int b : blocks) {
+            trial.k = k;
+            trial.block = b;
+            double ms_sum = 0.0;
+            for (int rep = 0; rep < 2; ++rep) {   // first run warms the graph cache
+                pch_stats st{};
+                pch_status rc = solve_instances(&m, 1, &sd, 1, &trial, nullptr, kOutNone, &st);
+                if (rc != PCH_OK) return rc;
+                if (rep == 1) ms_sum = st.ms_total;
+            }
+            if (ms_sum < best) { best = ms_sum; best_k = k; best_b = b; }
+        }
+    }
+    opt->k = best_k;
+    opt->block = best_b;
+    if (best_ms) *best_ms = best;
+    if (cache_path) {
+        std::ofstream out(cache_path, std::ios::app);
+        out << key << " " << best_k << " " << best_b << " " << best << "\n";
+    }
     return PCH_OK;
 }

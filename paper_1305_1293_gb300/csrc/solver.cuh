@@ -19,6 +19,8 @@ struct SolveCfg {
     int key_bits;
     int trim;
     int unroll;
+    int full_fan;
+    int profile;
     int pad;
     const float* mlp;
 };

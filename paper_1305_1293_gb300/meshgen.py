@@ -303,7 +303,7 @@ def torus(nu: int, nv: int, R: float = 1.0, r: float = 0.3, jitter: float = 0.4,
 # ----------------------------------------------------------------------------- closed-form solids
 def flat_patch(n: int, jitter: float = 0.3, seed: int = 0, size: float = 1.0) -> Mesh:
     """Convex square [0,size]^2 in the plane z=0, n x n quads, interior vertices jittered,
-    random diagonals.  Geodesic distance = Euclidean distance."""
+    random diagonals, no folded triangle.  Geodesic distance = Euclidean distance."""
     rng = SplitMix64(seed)
     h = size / n
     x, y = np.meshgrid(np.arange(n + 1) * h, np.arange(n + 1) * h, indexing="xy")
@@ -311,8 +311,12 @@ def flat_patch(n: int, jitter: float = 0.3, seed: int = 0, size: float = 1.0) ->
     i, j = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="xy")
     inner = ((i > 0) & (i < n) & (j > 0) & (j < n)).ravel()
     k = int(inner.sum())
-    x[inner] += rng.uniform(k, -jitter, jitter) * h
-    y[inner] += rng.uniform(k, -jitter, jitter) * h
+    # jitter inside a disk of radius jitter*h: with jitter < 0.35 no triangle can fold
+    # (each vertex-to-opposite-side height, >= h/sqrt(2), shrinks by at most 2*jitter*h)
+    rho = np.sqrt(rng.uniform(k)) * jitter * h
+    th = rng.uniform(k, 0.0, 2 * math.pi)
+    x[inner] += rho * np.cos(th)
+    y[inner] += rho * np.sin(th)
     v = np.stack([x, y, np.zeros_like(x)], 1)
     m = terrain(n, n, seed=seed + 1)  # reuse connectivity (random diagonals)
     return _finish(v, m.faces, f"flat{n}")

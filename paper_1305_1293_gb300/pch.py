@@ -18,7 +18,8 @@ PCH_OK, PCH_ERR_INVALID_ARG, PCH_ERR_NONMANIFOLD, PCH_ERR_DEGENERATE = 0, 1, 2, 
 PCH_ERR_OOM, PCH_ERR_CUDA, PCH_ERR_CAPACITY, PCH_ERR_TIMEOUT = 4, 5, 6, 7
 CONTROL_PLAIN, CONTROL_LEARNED, CONTROL_STRIDED = 0, 1, 2
 LOOP_GRAPH, LOOP_HOST = 0, 1
-FLAG_NO_TRIM, FLAG_FULL_FAN, FLAG_TRACE = 1, 2, 4
+FLAG_NO_TRIM, FLAG_FULL_FAN, FLAG_TRACE, FLAG_PROFILE = 1, 2, 4, 8
+PHASES = ("select", "propagate", "fan", "sort", "append", "control")
 
 _STATUS = {1: "INVALID_ARG", 2: "NONMANIFOLD", 3: "DEGENERATE", 4: "OOM", 5: "CUDA", 6: "CAPACITY", 7: "TIMEOUT"}
 
@@ -43,10 +44,13 @@ class Options(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("windows_created", ctypes.c_int64),
                 ("windows_propagated", ctypes.c_int64), ("peak_pending", ctypes.c_int64),
-                ("ms_total", ctypes.c_double), ("ms_setup", ctypes.c_double), ("bytes_workspace", ctypes.c_int64)]
+                ("ms_total", ctypes.c_double), ("ms_setup", ctypes.c_double), ("bytes_workspace", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 6)]
 
     def as_dict(self):
-        return {f[0]: getattr(self, f[0]) for f in self._fields_}
+        d = {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "ms_phase"}
+        d["ms_phase"] = dict(zip(PHASES, list(self.ms_phase)))
+        return d
 
 
 def _load():
@@ -70,6 +74,7 @@ def _load():
         "pch_mlp_adam": (I32, [P, P, P, P, I32, ctypes.c_float, P]),
         "pch_trace_fetch": (I32, [P, I32, P, P, P]),
         "pch_measure_fp64_peak": (I32, [P]),
+        "pch_autotune": (I32, [P, P, P, ctypes.c_char_p, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -226,3 +231,13 @@ def measure_fp64_peak() -> float:
     t = ctypes.c_double()
     _check(lib.pch_measure_fp64_peak(ctypes.byref(t)))
     return t.value
+
+
+def autotune(mesh: Mesh, source: int, cache_path: str | None = None, **opts):
+    """Fastest (k, block) for this mesh and source; returns (k, block, ms)."""
+    src = make_source(source)
+    o = make_options(**opts)
+    ms = ctypes.c_double()
+    _check(lib.pch_autotune(mesh.handle, ctypes.byref(src), ctypes.byref(o),
+                            cache_path.encode() if cache_path else None, ctypes.byref(ms)))
+    return int(o.k), int(o.block), ms.value

@@ -1,0 +1,121 @@
+"""Selection controller: the FP64 CPU reference is pinned by finite differences (no GPU);
+the GPU forward / backward / Adam kernels match it (gpu)."""
+import numpy as np
+import pytest
+
+from oracle import mlp_oracle as mo
+from paper_1305_1293_gb300.meshgen import SplitMix64
+
+
+def _data(n, seed=3):
+    rng = SplitMix64(seed)
+    X = rng.normal(n * mo.N_FEATURES).reshape(n, mo.N_FEATURES)
+    t = rng.normal(n)
+    return X, t
+
+
+def test_param_count():
+    assert mo.N_PARAMS == 64 * 24 + 64 + 2 * (64 * 64 + 64) + 64 + 1
+
+
+def test_backward_matches_central_differences():
+    """The hand-derived backward pass against (L(p + h e_i) - L(p - h e_i)) / 2h."""
+    p = mo.init_params(1)
+    rng = SplitMix64(9)
+    p = p + 0.05 * rng.normal(p.size)          # nonzero biases, W4 away from 0
+    X, t = _data(37)
+    g = mo.grad(p, X, t)
+    idx = np.unique(np.concatenate([np.arange(0, mo.N_PARAMS, 97), [mo.N_PARAMS - 1, mo.N_PARAMS - 65]]))
+    h = 1e-6
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = h
+        fd = (mo.loss(p + e, X, t) - mo.loss(p - e, X, t)) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)) + 1e-9, i
+
+
+def test_forward_special_cases():
+    """All-zero weights give y = b4; a single active path is a product of weights."""
+    p = np.zeros(mo.N_PARAMS)
+    p[-1] = 0.75
+    X, _ = _data(5)
+    assert np.allclose(mo.forward(p, X)[0], 0.75)
+    q = mo.unpack(np.zeros(mo.N_PARAMS))
+    q["W1"][0, 2] = 2.0
+    q["W2"][0, 0] = 3.0
+    q["W3"][0, 0] = 0.5
+    q["W4"][0] = -1.0
+    pp = mo.pack(q)
+    x = np.zeros((2, mo.N_FEATURES))
+    x[0, 2], x[1, 2] = 1.5, -1.0      # second sample blocked by the first ReLU
+    y, _ = mo.forward(pp, x)
+    assert np.allclose(y, [-(2.0 * 1.5) * 3.0 * 0.5, 0.0])
+
+
+def test_adam_reduces_loss_cpu():
+    p = mo.init_params(2)
+    X, _ = _data(64, 5)
+    t = X[:, 0] * 0.5 - X[:, 3]
+    m = np.zeros_like(p)
+    v = np.zeros_like(p)
+    l0 = mo.loss(p, X, t)
+    for k in range(1, 201):
+        p, m, v = mo.adam_step(p, mo.grad(p, X, t), m, v, k, 1e-2)
+    assert mo.loss(p, X, t) < 0.2 * l0
+
+
+# ------------------------------------------------------------------ GPU kernels
+@pytest.fixture(scope="module")
+def gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1293_gb300 import pch
+    return torch, pch
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("n", [1, 37, 1000])
+def test_gpu_forward_backward_match_cpu(gpu, n):
+    torch, pch = gpu
+    p = (mo.init_params(4) + 0.05 * SplitMix64(11).normal(mo.N_PARAMS)).astype(np.float32)
+    X, t = _data(n, 6)
+    X, t = X.astype(np.float32), t.astype(np.float32)
+    dev = "cuda"
+    pd, xd, td = (torch.from_numpy(a).to(dev) for a in (p, X, t))
+    y = torch.empty(n, dtype=torch.float32, device=dev)
+    g = torch.empty(mo.N_PARAMS, dtype=torch.float32, device=dev)
+    l = torch.empty(1, dtype=torch.float32, device=dev)
+    pch.mlp_forward(pd, xd, y)
+    pch.mlp_backward(pd, xd, td, g, l)
+    torch.cuda.synchronize()
+    p64, X64, t64 = p.astype(np.float64), X.astype(np.float64), t.astype(np.float64)
+    y_ref = mo.forward(p64, X64)[0]
+    g_ref = mo.grad(p64, X64, t64)
+    assert np.max(np.abs(y.cpu().numpy() - y_ref)) <= 1e-4 * max(1.0, np.abs(y_ref).max())
+    gg = g.cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(gg - g_ref)) <= 1e-4 * max(1e-3, np.abs(g_ref).max())
+    assert abs(l.item() - mo.loss(p64, X64, t64)) <= 1e-4 * max(1.0, mo.loss(p64, X64, t64))
+    # deterministic reduction: bit-identical on a second call
+    g2 = torch.empty_like(g)
+    pch.mlp_backward(pd, xd, td, g2, l)
+    torch.cuda.synchronize()
+    assert torch.equal(g, g2)
+
+
+@pytest.mark.gpu
+def test_gpu_adam_matches_cpu(gpu):
+    torch, pch = gpu
+    p = mo.init_params(5).astype(np.float32)
+    g = SplitMix64(3).normal(mo.N_PARAMS).astype(np.float32)
+    m = np.zeros(mo.N_PARAMS, dtype=np.float32)
+    v = np.zeros(mo.N_PARAMS, dtype=np.float32)
+    pd, gd, md, vd = (torch.from_numpy(a.copy()).cuda() for a in (p, g, m, v))
+    pc, mc, vc = p.astype(np.float64), m.astype(np.float64), v.astype(np.float64)
+    for t in (1, 2, 3):
+        pch.mlp_adam(pd, gd, md, vd, t, 1e-3)
+        pc, mc, vc = mo.adam_step(pc, g.astype(np.float64), mc, vc, t, 1e-3)
+    torch.cuda.synchronize()
+    assert np.max(np.abs(pd.cpu().numpy() - pc)) < 1e-6

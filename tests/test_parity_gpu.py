@@ -121,12 +121,17 @@ def test_result_independent_of_k(pch, oracle_lib, k):
     assert max_rel(got, ref) < TOL
 
 
-def test_no_trim_same_result(pch, oracle_lib):
-    m = mg.geodesic_sphere(9, 0.02, seed=5)
-    ref, _ = oracle_lib.geodesic(m.vertices, m.faces, 3)
-    a, _ = gpu_solve(pch, m, 3)
-    b, _ = gpu_solve(pch, m, 3, flags=pch.FLAG_NO_TRIM)
-    assert max_rel(a, ref) < TOL and max_rel(b, ref) < TOL
+@pytest.mark.parametrize("flags", ["NO_TRIM", "FULL_FAN", "NO_TRIM|FULL_FAN"])
+def test_variants_same_result(pch, oracle_lib, flags):
+    """Trimming and the fanned-area restriction remove only useless windows."""
+    fl = 0
+    for f in flags.split("|"):
+        fl |= getattr(pch, "FLAG_" + f)
+    for m, s in ((mg.geodesic_sphere(9, 0.02, seed=5), 3), (mg.terrain(20, 17, seed=6, amp_range=(1, 6)), 180)):
+        ref, _ = oracle_lib.geodesic(m.vertices, m.faces, s)
+        a, sa = gpu_solve(pch, m, s)
+        b, sb = gpu_solve(pch, m, s, flags=fl)
+        assert max_rel(a, ref) < TOL and max_rel(b, ref) < TOL
 
 
 def test_face_point_source_vs_oracle(pch, oracle_lib):
