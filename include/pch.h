@@ -74,13 +74,15 @@ enum {
 typedef struct {
     int32_t control;          /* PCH_CONTROL_* */
     int32_t loop;             /* PCH_LOOP_* */
-    int64_t k;                /* PLAIN/STRIDED: windows selected per instance per iteration */
+    int64_t k;                /* PLAIN/STRIDED: windows selected per instance per iteration
+                                 (default 24576, the paper's 24 * 2^10) */
     int64_t max_iters;        /* iteration cap; exceeded -> PCH_ERR_TIMEOUT (default 2^31) */
     void* stream;             /* cudaStream_t to run on (NULL = legacy default stream) */
     int32_t out_on_device;    /* nonzero: output pointers are device pointers */
     int32_t block;            /* threads per block of the propagation kernel (0 = tuned) */
     int32_t flags;            /* PCH_FLAG_* */
-    int32_t reserved;
+    int32_t hops;             /* windows one propagation lane may chain within an iteration's
+                                 band (1 = the paper's one hop per iteration; 0 = default) */
 } pch_options;
 
 enum {
@@ -104,6 +106,10 @@ typedef struct {
     int64_t kernel_launches;      /* CUDA kernels this call launched */
     double ms_phase[6];           /* PCH_FLAG_PROFILE: selection (tau + compaction), propagation,
                                      fans, sort, append, loop control; else 0 */
+    int64_t fans;                 /* pseudo-source fans built */
+    int64_t fan_windows;          /* windows those fans created */
+    int64_t fan_candidates;       /* distance events at pseudo-source vertices examined */
+    int64_t windows_chained;      /* children propagated in the same iteration (hops > 1) */
 } pch_stats;
 
 /* Build a mesh: host arrays `vertices` (n_vertices x 3 doubles, xyz) and `faces`
@@ -169,10 +175,10 @@ pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float
                            int32_t* n_rows);
 
 /* ---- autotuner (build-only) ------------------------------------------------------------
- * Times full solves of `src` on `m` over a grid of windows-per-iteration k (powers of 4
- * from 4096 up to the mesh's face count) and propagation block sizes (128, 256, 512),
- * and writes the fastest into opt->k and opt->block (the other fields of *opt are kept
- * and used for every trial).  If cache_path is not NULL the result is looked up first
+ * Times full solves of `src` on `m` over a grid of windows-per-iteration k (24576 times
+ * powers of 4, up to 8x the face count), propagation block sizes (128, 256) and hops
+ * (1, 2, 4, 8), and writes the fastest into opt->k, opt->block and opt->hops (the other
+ * fields of *opt are kept and used for every trial).  If cache_path is not NULL the result is looked up first
  * in, and then appended to, that text file, keyed by GPU name and mesh size, so a
  * second call does no timing.  Errors: as pch_solve. */
 pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_options* opt, const char* cache_path,

@@ -22,7 +22,16 @@ long long default_k() {
         long long v = std::atoll(e);
         if (v > 0) return v;
     }
-    return 32768;
+    return 24576;   // the paper's tuned range 16*2^10 .. 24*2^10 (Section 5.2)
+}
+
+int default_hops() {
+    const char* e = std::getenv("PCH_DEFAULT_HOPS");
+    if (e) {
+        int v = std::atoi(e);
+        if (v > 0) return v;
+    }
+    return 4;
 }
 
 // ---------------------------------------------------------------- training kernels

@@ -119,6 +119,9 @@ struct Counters {
     int sort_bits;          // bits of the sort key
     int halt;               // set by k_finish when the loop must stop; every kernel no-ops
     unsigned long long created, propagated, filtered, trimmed, peak_pending;
+    unsigned long long fans, fan_windows, fan_cand, chained;
+    int work_next;          // next work-list index handed to a propagation lane
+    int pad2;
 };
 
 enum : int {

@@ -370,159 +370,221 @@ __device__ __forceinline__ double child_key(double d, double a, double b, double
     return d + (Ipx < a ? IA : (Ipx > b ? IB : -Ipy));
 }
 
-__global__ void __launch_bounds__(256) k_propagate(Work w) {
+// dominated(lhs, rhs) with rhs = g + sqrt(q): compares squares, no square root.
+constexpr double kInvDom = 1.0 / (1.0 + kDomRel);
+__device__ __forceinline__ bool dominated_sq(double lhs, double g, double q) {
+    const double t = lhs * kInvDom - g;
+    return t > 0.0 && t * t > q;
+}
+
+// Algorithm 2 for one window: events, one angle one split, children with the Xin-Wang
+// filter.  Returns whether the window passed the filter; children in c0, c1 (nch).
+__device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, int2* req, double2* req_d, int inst,
+                                                 int src, double d, int h, double A, double B, double px, double py,
+                                                 ChildOut& c0, ChildOut& c1, int& nch) {
+    bool prop = false;
+    nch = 0;
+        {
+        const Inst& I = w.inst[inst];
+        const HERec R = I.rec[h];
+        const double L = R.L;
+        double g0 = ldg_dist(I.g, R.v0 & ~kPseudoBit);
+        double g1 = ldg_dist(I.g, R.v1 & ~kPseudoBit);
+        double g2 = ldg_dist(I.g, R.v2 & ~kPseudoBit);
+        const double py2 = py * py;
+        const double ax = A - px, bx = B - px;
+        const double IA = sqrt(ax * ax + py2), IB = sqrt(bx * bx + py2);
+        // Xin-Wang endpoint tests against the current distances: the window is
+        // useless if the path via v0 beats it at B, or the path via v1 at A.
+        if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)) || stale_source(I, src, d))) {
+            prop = true;
+            const double tol = kEpsSnap * L;
+            // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
+            if (A <= tol) {
+                double D0 = d + (A == 0.0 ? IA : sqrt(px * px + py2));
+                if (vertex_event(I, R.v0, D0, g0)) {
+                    // the ray arrives at v0 through the twin face: direction to I
+                    const unsigned v = R.v0 & ~kPseudoBit;
+                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D0,
+                             wrap_angle(I, v, I.vphi[h] + atan2(py, px)));
+                }
+            }
+            if (B >= L - tol) {
+                double q = L - px;
+                double D1 = d + (B == L ? IB : sqrt(q * q + py2));
+                if (vertex_event(I, R.v1, D1, g1)) {
+                    const unsigned v = R.v1 & ~kPseudoBit;
+                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D1,
+                             wrap_angle(I, v, I.vphi[R.twin] + atan2(py, -q) + 3.14159265358979323846));
+                }
+            }
+            // occupancy of v2: the ray I -> v2 crosses e at xs = px + num / den;
+            // decided without the division (den > 0)
+            const double xc = R.xc, yc = R.yc;
+            const double den = yc - py, num = (xc - px) * (-py);
+            const bool before_A = num < (A - tol - px) * den;
+            const bool occ = !before_A && num <= (B + tol - px) * den;
+            bool left, right;
+            double Iv2 = 0.0, xcl = 0.0;
+            if (occ) {
+                const double xs = px + num / den;
+                xcl = fmin(fmax(xs, A), B);
+                const double dx = xc - px, dy = yc - py;
+                Iv2 = sqrt(dx * dx + dy * dy);
+                const double D2 = d + Iv2;
+                // one angle one split (Fig. `fig:filter`(a)) against angle_split[h]
+                unsigned long long* ap = I.ang + h;
+                const unsigned long long aw = __ldcg(ap);
+                bool win = aw == kEmptyAngle || D2 < bitsd(aw & ~kAngleXMask);
+                if (win) {
+                    left = right = true;
+                    atomicMin(ap, pack_angle(D2, xs, R.iL));
+                } else {
+                    // loser: keep the child on its own side of the winner's ray
+                    const double q = (double)(aw & kAngleXMask);
+                    const double sc = L * (1.0 / (double)(1 << kAngleXBits));
+                    left = xs < q * sc - tol;
+                    right = xs > (q + 1.0) * sc + tol;
+                    if (!left && !right) left = right = true;
+                }
+                if (vertex_event(I, R.v2, D2, g2)) {
+                    // the ray arrives at v2 inside face(h): angle from v2->v0 towards I
+                    const unsigned v = R.v2 & ~kPseudoBit;
+                    const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
+                    double da = atan2(py - yc, px - xc) - atan2(-yc, -xc);
+                    if (da < 0.0) da += 2.0 * 3.14159265358979323846;
+                    da = fmin(da, I.hang[hp]);
+                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D2,
+                             wrap_angle(I, v, I.vphi[hp] + da));
+                }
+                if (B - xcl <= kEpsTiny * L) right = false;
+                if (xcl - A <= kEpsTiny * L) left = false;
+            } else {
+                right = before_A;
+                left = !right;
+            }
+            right = right && R.tw1 >= 0;
+            left = left && R.tw2 >= 0;
+            // Children, one code path in child order (right first): the right child
+            // lies on edge v2 -> v1 (frame origin v2), the left on v0 -> v2 (origin v0).
+            // When v2 is occupied the child's endpoint at v2 is exact.
+#pragma unroll 1
+            for (int j = 0; j < 2; ++j) {
+                if (!(j == 0 ? (right || left) : (right && left))) break;
+                const bool rt = j == 0 && right;
+                const double Lc = rt ? R.L1 : R.L2;
+                const double ox = rt ? xc : 0.0, oy = rt ? yc : 0.0;
+                const double ux = rt ? (L - xc) * R.iL1 : xc * R.iL2;
+                const double uy = rt ? -yc * R.iL1 : yc * R.iL2;
+                const double rx = px - ox, ry = py - oy;
+                const double Ipx = rx * ux + ry * uy, Ipy = ux * ry - uy * rx;
+                // rays through A and B; at v2 (occupied) the right child starts at 0,
+                // the left child ends at Lc
+                double a, IAc, b, IBc;
+                if (occ && rt) {
+                    a = 0.0;
+                    IAc = Iv2;
+                } else {
+                    const double qx = A - ox;
+                    ray_hit(Ipx, Ipy, qx * ux - oy * uy, -ux * oy - uy * qx, IA, Lc, a, IAc);
+                }
+                if (occ && !rt) {
+                    b = Lc;
+                    IBc = Iv2;
+                } else {
+                    const double qx = B - ox;
+                    ray_hit(Ipx, Ipy, qx * ux - oy * uy, -ux * oy - uy * qx, IB, Lc, b, IBc);
+                }
+                if (!(b - a > kEpsTiny * Lc)) continue;
+                // Xin-Wang filter (Fig. `fig:filter`(b)) on the new window: against its
+                // start and end vertices, and against the vertex of the parent edge that
+                // is not on the child's edge (tested at the endpoint nearer the shared one).
+                bool useless;
+                if (rt) {   // start v2, end v1, third vertex v0 tested at b
+                    const double Xx = xc + b * ux, Xy = yc + b * uy;
+                    useless = dominated(d + IBc, g2 + b) || dominated(d + IAc, g1 + (Lc - a)) ||
+                              dominated_sq(d + IBc, g0, Xx * Xx + Xy * Xy);
+                } else {    // start v0, end v2, third vertex v1 tested at a
+                    const double Xx = a * ux - L, Xy = a * uy;
+                    useless = dominated(d + IBc, g0 + b) || dominated(d + IAc, g2 + (Lc - a)) ||
+                              dominated_sq(d + IAc, g1, Xx * Xx + Xy * Xy);
+                }
+                if (useless) continue;
+                const ChildOut co{rt ? R.tw1 : R.tw2, a, b, Ipx, Ipy, child_key(d, a, b, Ipx, Ipy, IAc, IBc)};
+                if (nch == 0) c0 = co;
+                else c1 = co;
+                ++nch;
+            }
+        }
+    }
+    return prop;
+}
+
+// Persistent propagation over the work list.  Lanes without a window take the next one
+// from a warp-aggregated counter; a lane whose window produced a child with key inside
+// this iteration's band (key <= tau) propagates that child at once, up to `hops`
+// windows per chain, while the child arena stays below half full.
+__global__ void __launch_bounds__(256) k_propagate(Work w, int hops) {
     Counters* cnt = w.cnt;
     if (cnt->halt) return;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int it = cnt->iter;
     const int n = min(cnt->n_sel, w.sel_cap);
     int2* req = w.req[it & 1];
     double2* req_d = w.req_d[it & 1];
-    for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
-        const int i = base + threadIdx.x;
-        ChildOut c[2];
-        int nc = 0, inst = 0, src = -1;
-        double d = 0.0;
-        bool prop = false;
-        if (i < n) {
-            const int h = w.sel.he[i];
-            inst = w.sel.inst[i];
-            d = w.sel.d[i];
-            src = w.sel.src[i];
-            const double A = w.sel.A[i], B = w.sel.B[i], px = w.sel.px[i], py = w.sel.py[i];
-            const Inst& I = w.inst[inst];
-            const HERec R = I.rec[h];
-            const double L = R.L;
-            double g0 = ldg_dist(I.g, R.v0 & ~kPseudoBit);
-            double g1 = ldg_dist(I.g, R.v1 & ~kPseudoBit);
-            double g2 = ldg_dist(I.g, R.v2 & ~kPseudoBit);
-            const double py2 = py * py;
-            const double ax = A - px, bx = B - px;
-            const double IA = sqrt(ax * ax + py2), IB = sqrt(bx * bx + py2);
-            // Xin-Wang endpoint tests against the current distances: the window is
-            // useless if the path via v0 beats it at B, or the path via v1 at A.
-            if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)) || stale_source(I, src, d))) {
-                prop = true;
-                const double tol = kEpsSnap * L;
-                // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
-                if (A <= tol) {
-                    double D0 = d + (A == 0.0 ? IA : sqrt(px * px + py2));
-                    if (vertex_event(I, R.v0, D0, g0)) {
-                        // the ray arrives at v0 through the twin face: direction to I
-                        const unsigned v = R.v0 & ~kPseudoBit;
-                        push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D0,
-                                 wrap_angle(I, v, I.vphi[h] + atan2(py, px)));
-                    }
-                }
-                if (B >= L - tol) {
-                    double q = L - px;
-                    double D1 = d + (B == L ? IB : sqrt(q * q + py2));
-                    if (vertex_event(I, R.v1, D1, g1)) {
-                        const unsigned v = R.v1 & ~kPseudoBit;
-                        push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D1,
-                                 wrap_angle(I, v, I.vphi[R.twin] + atan2(py, -q) + 3.14159265358979323846));
-                    }
-                }
-                // occupancy of v2: the ray I -> v2 crosses e at xs
-                const double xc = R.xc, yc = R.yc;
-                const double xs = px + (xc - px) * (-py) / (yc - py);
-                const bool occ = (xs >= A - tol) && (xs <= B + tol);
-                const double xcl = fmin(fmax(xs, A), B);
-                bool left, right;
-                double Iv2 = 0.0;
-                if (occ) {
-                    const double dx = xc - px, dy = yc - py;
-                    Iv2 = sqrt(dx * dx + dy * dy);
-                    const double D2 = d + Iv2;
-                    // one angle one split (Fig. `fig:filter`(a)) against angle_split[h]
-                    unsigned long long* ap = I.ang + h;
-                    const unsigned long long aw = __ldcg(ap);
-                    bool win = aw == kEmptyAngle || D2 < bitsd(aw & ~kAngleXMask);
-                    if (win) {
-                        left = right = true;
-                        atomicMin(ap, pack_angle(D2, xs, R.iL));
-                    } else {
-                        // loser: keep the child on its own side of the winner's ray
-                        const double q = (double)(aw & kAngleXMask);
-                        const double sc = L * (1.0 / (double)(1 << kAngleXBits));
-                        left = xs < q * sc - tol;
-                        right = xs > (q + 1.0) * sc + tol;
-                        if (!left && !right) left = right = true;
-                    }
-                    if (vertex_event(I, R.v2, D2, g2)) {
-                        // the ray arrives at v2 inside face(h): angle from v2->v0 towards I
-                        const unsigned v = R.v2 & ~kPseudoBit;
-                        const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
-                        double da = atan2(py - yc, px - xc) - atan2(-yc, -xc);
-                        if (da < 0.0) da += 2.0 * 3.14159265358979323846;
-                        da = fmin(da, I.hang[hp]);
-                        push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D2,
-                                 wrap_angle(I, v, I.vphi[hp] + da));
-                    }
-                    if (B - xcl <= kEpsTiny * L) right = false;
-                    if (xcl - A <= kEpsTiny * L) left = false;
-                } else {
-                    right = xs < A;
-                    left = !right;
-                }
-                if (right && R.tw1 >= 0) {
-                    // child on edge v2 -> v1 (twin of next(h)): frame origin v2
-                    const double L1 = R.L1;
-                    const double ux = (L - xc) * R.iL1, uy = -yc * R.iL1;
-                    const double rx = px - xc, ry = py - yc;
-                    const double Ipx = rx * ux + ry * uy, Ipy = ux * ry - uy * rx;
-                    double a, IAc, b, IBc;
-                    if (occ) {
-                        a = 0.0;
-                        IAc = Iv2;
-                    } else {
-                        const double qx = A - xc;
-                        ray_hit(Ipx, Ipy, qx * ux - yc * uy, -ux * yc - uy * qx, IA, L1, a, IAc);
-                    }
-                    {
-                        const double qx = B - xc;
-                        ray_hit(Ipx, Ipy, qx * ux - yc * uy, -ux * yc - uy * qx, IB, L1, b, IBc);
-                    }
-                    if (b - a > kEpsTiny * L1) {
-                        const double Xx = xc + b * ux, Xy = yc + b * uy;      // X_B in h's frame
-                        const double v0X = sqrt(Xx * Xx + Xy * Xy);
-                        // Xin-Wang filter (Fig. `fig:filter`(b)) on the new window
-                        if (!(dominated(d + IBc, g2 + b) || dominated(d + IAc, g1 + (L1 - a)) ||
-                              dominated(d + IBc, g0 + v0X))) {
-                            c[nc++] = ChildOut{R.tw1, a, b, Ipx, Ipy, child_key(d, a, b, Ipx, Ipy, IAc, IBc)};
-                        }
-                    }
-                }
-                if (left && R.tw2 >= 0) {
-                    // child on edge v0 -> v2 (twin of prev(h)): frame origin v0
-                    const double L2 = R.L2;
-                    const double ux = xc * R.iL2, uy = yc * R.iL2;
-                    const double Ipx = px * ux + py * uy, Ipy = ux * py - uy * px;
-                    double a, IAc, b, IBc;
-                    ray_hit(Ipx, Ipy, A * ux, -uy * A, IA, L2, a, IAc);
-                    if (occ) {
-                        b = L2;
-                        IBc = Iv2;
-                    } else {
-                        ray_hit(Ipx, Ipy, B * ux, -uy * B, IB, L2, b, IBc);
-                    }
-                    if (b - a > kEpsTiny * L2) {
-                        const double Xx = a * ux - L, Xy = a * uy;            // X_A - v1 in h's frame
-                        const double v1X = sqrt(Xx * Xx + Xy * Xy);
-                        if (!(dominated(d + IBc, g0 + b) || dominated(d + IAc, g2 + (L2 - a)) ||
-                              dominated(d + IAc, g1 + v1X))) {
-                            c[nc++] = ChildOut{R.tw2, a, b, Ipx, Ipy, child_key(d, a, b, Ipx, Ipy, IAc, IBc)};
-                        }
-                    }
+    const int room = w.arena_cap / 2 - 2 * (int)(gridDim.x * blockDim.x);
+    bool have = false, exhausted = false;
+    int h = 0, inst = 0, src = -1, hop = 0;
+    double d = 0.0, A = 0.0, B = 0.0, px = 0.0, py = 0.0;
+    while (true) {
+        const unsigned need = __ballot_sync(full, !have);
+        if (need && !exhausted) {
+            int base = 0;
+            if (lane == 0) base = atomicAdd(&cnt->work_next, __popc(need));
+            base = __shfl_sync(full, base, 0);
+            if (base >= n) exhausted = true;
+            if (!have) {
+                const int idx = base + __popc(need & lt);
+                if (idx < n) {
+                    h = w.sel.he[idx]; inst = w.sel.inst[idx]; d = w.sel.d[idx]; src = w.sel.src[idx];
+                    A = w.sel.A[idx]; B = w.sel.B[idx]; px = w.sel.px[idx]; py = w.sel.py[idx];
+                    have = true;
+                    hop = 0;
                 }
             }
         }
-        int slot = warp_reserve(&cnt->n_child, nc);
-        for (int j = 0; j < nc; ++j) {
-            int s = slot + j;
-            if (s < w.arena_cap) store_win(w.arena, s, c[j].he, inst, d, c[j].A, c[j].B, c[j].px, c[j].py, c[j].key, src);
-            else atomicOr(&cnt->error, kErrPoolFull);
+        if (!__any_sync(full, have)) break;
+        ChildOut c0, c1;
+        int nch = 0;
+        bool prop = false;
+        if (have) prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, c0, c1, nch);
+        bool cont = have && nch > 0 && hop + 1 < hops && c0.key <= w.ctl[inst].tau &&
+                    *(volatile int*)&cnt->n_child < room;
+        const int nwrite = have ? (cont ? nch - 1 : nch) : 0;
+        const int slot = warp_reserve(&cnt->n_child, nwrite);
+        if (cont) {
+            if (nch > 1) {
+                if (slot < w.arena_cap) store_win(w.arena, slot, c1.he, inst, d, c1.A, c1.B, c1.px, c1.py, c1.key, src);
+                else atomicOr(&cnt->error, kErrPoolFull);
+            }
+            h = c0.he; A = c0.A; B = c0.B; px = c0.px; py = c0.py;
+            ++hop;
+        } else if (have) {
+            if (nch > 0) {
+                if (slot < w.arena_cap) store_win(w.arena, slot, c0.he, inst, d, c0.A, c0.B, c0.px, c0.py, c0.key, src);
+                else atomicOr(&cnt->error, kErrPoolFull);
+            }
+            if (nch > 1) {
+                if (slot + 1 < w.arena_cap)
+                    store_win(w.arena, slot + 1, c1.he, inst, d, c1.A, c1.B, c1.px, c1.py, c1.key, src);
+                else atomicOr(&cnt->error, kErrPoolFull);
+            }
+            have = false;
         }
         warp_add_ull(&cnt->propagated, prop ? 1 : 0);
+        warp_add_ull(&cnt->chained, cont ? 1 : 0);
     }
 }
 
@@ -585,54 +647,77 @@ __device__ __forceinline__ double fan_hit(const HERec& Ro, double beta) {
     return fmin(fmax(s, 0.0), Ro.L);
 }
 
-__global__ void k_fan(Work w, int full_fan) {
+// One warp per fan candidate; lane j handles face j of the vertex's one-ring.
+__global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
     Counters* cnt = w.cnt;
     if (cnt->halt) return;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
     const int it = cnt->iter;
     const int nreq = min(cnt->n_req, w.req_cap);
+    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cnt->fan_cand, (unsigned long long)nreq);
     const int2* req = w.req[it & 1];
     const double2* req_d = w.req_d[it & 1];
     int2* req_nx = w.req[(it + 1) & 1];
     double2* req_d_nx = w.req_d[(it + 1) & 1];
     const unsigned stamp_fan = (unsigned)it + 1u;
-    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < nreq; r += gridDim.x * blockDim.x) {
+    const int warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int r = warp0; r < nreq; r += nwarps) {
         const int inst = req[r].x;
         const unsigned v = (unsigned)req[r].y;
         const double D = req_d[r].x, phi = req_d[r].y;
         const Inst& I = w.inst[inst];
-        if (dbits(D) != __ldcg(I.g + v)) continue;                  // superseded by a shorter event
-        if (atomicExch(I.stamp + v, stamp_fan) == stamp_fan) continue;   // one fan per vertex per iteration
+        int ok = 0;
+        if (lane == 0) {
+            // still the vertex's distance (not superseded), and the first fan this iteration
+            ok = dbits(D) == __ldcg(I.g + v) && atomicExch(I.stamp + v, stamp_fan) != stamp_fan;
+            if (ok) atomicAdd(&cnt->fans, 1ull);
+        }
+        if (!__shfl_sync(full, ok, 0)) continue;
         const int s = I.vstart[v], e = I.vstart[v + 1];
         const double T = I.vtheta[v];
         const Wedges W = make_wedges(I.vflag[v] & 1, T, phi, full_fan != 0);
         if (W.n == 0) continue;
-        // pass 1: windows this fan creates
-        int count = 0;
-        for (int j = s; j < e; ++j) {
-            const int hv = I.vlist[j];
-            double b0, b1;
-            if (wedge_part(W, T, I.vphi[hv], I.hang[hv], b0, b1) && I.rec[he_next(hv)].twin >= 0) ++count;
-        }
-        const int base = atomicAdd(&cnt->n_child, count);
-        if (base + count > w.arena_cap) {
-            // no room this iteration: mark the reserved slots empty and retry next iteration
-            for (int j = base; j < min(base + count, w.arena_cap); ++j) w.arena.he[j] = -1;
-            atomicExch(I.stamp + v, 0u);
-            push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, v, D, phi);
-            continue;
-        }
-        int slot = base;
-        for (int j = s; j < e; ++j) {
-            const int hv = I.vlist[j];
-            double b0, b1;
-            const double c = I.hang[hv];
-            if (!wedge_part(W, T, I.vphi[hv], c, b0, b1)) continue;
-            const int o = he_next(hv);                 // edge (a -> b) opposite v
-            const HERec Ro = I.rec[o];
+        bool deferred = false;
+        for (int j0 = s; j0 < e && !deferred; j0 += 32) {
+            const int j = j0 + lane;
+            double b0 = 0.0, b1 = 0.0, c = 0.0;
+            bool has = false;
+            int o = 0;
+            HERec Ro;
+            if (j < e) {
+                const int hv = I.vlist[j];
+                c = I.hang[hv];
+                has = wedge_part(W, T, I.vphi[hv], c, b0, b1);
+                if (has) {
+                    o = he_next(hv);                   // edge (a -> b) opposite v
+                    Ro = I.rec[o];
+                }
+            }
+            const bool win = has && Ro.twin >= 0;
+            const unsigned bal = __ballot_sync(full, win);
+            const int cntw = __popc(bal);
+            int base = 0;
+            if (lane == 0 && cntw) base = atomicAdd(&cnt->n_child, cntw);
+            base = __shfl_sync(full, base, 0);
+            if (base + cntw > w.arena_cap) {
+                // no room this iteration: mark the reserved slots empty, retry next iteration
+                const int sl = base + __popc(bal & lt);
+                if (win && sl < w.arena_cap) w.arena.he[sl] = -1;
+                if (lane == 0) {
+                    atomicExch(I.stamp + v, 0u);
+                    push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, v, D, phi);
+                }
+                deferred = true;
+                continue;
+            }
+            if (!has) continue;
             const double Lo = Ro.L;
             const double s0 = b0 <= 1e-12 ? 0.0 : fan_hit(Ro, b0);
             const double s1 = b1 >= c - 1e-12 ? Lo : fan_hit(Ro, b1);
-            if (Ro.twin < 0) {
+            if (!win) {
                 // boundary edge: endpoint events for the covered endpoints
                 const unsigned a = Ro.v0 & ~kPseudoBit, b = Ro.v1 & ~kPseudoBit;
                 double ga = ldg_dist(I.g, a), gb = ldg_dist(I.g, b);
@@ -645,8 +730,8 @@ __global__ void k_fan(Work w, int full_fan) {
                 continue;
             }
             // window on twin(o) = (b -> a): I = v at (Lo - xc, -yc), interval [Lo - s1, Lo - s0]
+            const int sl = base + __popc(bal & lt);
             const double A = Lo - s1, B = Lo - s0;
-            const int sl = slot++;
             const double px = Lo - Ro.xc, py = -Ro.yc;
             const double IA = sqrt((A - px) * (A - px) + py * py), IB = sqrt((B - px) * (B - px) + py * py);
             const double ga = ldg_dist(I.g, Ro.v0 & ~kPseudoBit), gb = ldg_dist(I.g, Ro.v1 & ~kPseudoBit);
@@ -656,6 +741,7 @@ __global__ void k_fan(Work w, int full_fan) {
             }
             const double key = D + (px < A ? IA : (px > B ? IB : -py));
             store_win(w.arena, sl, Ro.twin, inst, D, A, B, px, py, key, (int)v);
+            atomicAdd(&cnt->fan_windows, 1ull);
         }
     }
 }
@@ -741,6 +827,7 @@ __global__ void k_finish(Work w, cudaGraphConditionalHandle handle, int use_cond
         c->n_sel = 0;
         c->n_child = 0;
         c->n_app = 0;
+        c->work_next = 0;
         c->iter += 1;
         c->done = (np == 0 && c->n_req == 0) ? 1 : 0;
         if (!c->done && c->iter >= max_iters) c->error |= kErrIter;
@@ -958,7 +1045,7 @@ static int grid_for(int blocks_per_sm) { return sm_count() * blocks_per_sm; }
 // Kernels one iteration launches (for pch_stats.kernel_launches).
 static int kernels_per_iteration(const SolveCfg& cfg) {
     int passes = (cfg.key_bits + kRsDigitBits - 1) / kRsDigitBits;
-    return 7 + 3 * (passes < 1 ? 1 : passes);
+    return 6 + sort_kernels_per_pass() * (passes < 1 ? 1 : passes);
 }
 
 // Launch one iteration (all phases).  With `ev` (7 events) the phase boundaries are
@@ -971,9 +1058,9 @@ static cudaError_t launch_iteration(Workspace* ws, cudaStream_t s, const SolveCf
     k_tau<<<std::min(w.n_inst, 1024), 256, 0, s>>>(w, cfg.control, cfg.mlp);
     k_compact<<<grid_for(4), tpb, 0, s>>>(w);
     if (ev) cudaEventRecord(ev[1], s);
-    k_propagate<<<grid_for(cfg.prop_blocks_per_sm), cfg.prop_threads, 0, s>>>(w);
+    k_propagate<<<grid_for(cfg.prop_blocks_per_sm), cfg.prop_threads, 0, s>>>(w, cfg.hops);
     if (ev) cudaEventRecord(ev[2], s);
-    k_fan<<<grid_for(2), 128, 0, s>>>(w, cfg.full_fan);
+    k_fan<<<grid_for(2), 256, 0, s>>>(w, cfg.full_fan);
     if (ev) cudaEventRecord(ev[3], s);
     unsigned* kb[2] = {w.sort_key[0], w.sort_key[1]};
     int* vb[2] = {w.sort_val[0], w.sort_val[1]};
@@ -1105,6 +1192,10 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         stats->ms_total = ms;
         stats->bytes_workspace = (int64_t)(ws->pools.bytes + ws->inst_mem.bytes + ws->fixed.bytes);
         stats->kernel_launches += launches;
+        stats->fans = (int64_t)c.fans;
+        stats->fan_windows = (int64_t)c.fan_windows;
+        stats->fan_candidates = (int64_t)c.fan_cand;
+        stats->windows_chained = (int64_t)c.chained;
         for (int p = 0; p < 6; ++p) stats->ms_phase[p] = phase_ms[p];
     }
     return PCH_OK;
@@ -1121,6 +1212,7 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     cfg.trim = !(opt && (opt->flags & PCH_FLAG_NO_TRIM));
     cfg.full_fan = (opt && (opt->flags & PCH_FLAG_FULL_FAN)) ? 1 : 0;
     cfg.profile = (opt && (opt->flags & PCH_FLAG_PROFILE)) ? 1 : 0;
+    cfg.hops = (opt && opt->hops > 0) ? opt->hops : default_hops();
     cfg.unroll = 2;
     int bits = 1;
     while ((1LL << bits) <= total_keys) ++bits;   // invalid key ~0u must exceed all valid keys
@@ -1153,6 +1245,9 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
             return set_error(PCH_ERR_INVALID_ARG, "unknown source kind %d", sd.kind);
         }
     }
+    if (opt && opt->block != 0 && (opt->block < 32 || opt->block > 256 || opt->block % 32 != 0))
+        return set_error(PCH_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 256], got %d", opt->block);
+    if (opt && opt->k < 0) return set_error(PCH_ERR_INVALID_ARG, "k must be >= 0");
     cudaStream_t s = opt ? (cudaStream_t)opt->stream : (cudaStream_t)0;
     Workspace* ws;
     pch_status st = ensure_workspace(meshes[0], &ws);
@@ -1332,11 +1427,12 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
             std::istringstream ls(line);
             std::string k2;
             long long kk;
-            int bb;
+            int bb, hh;
             double ms;
-            if (ls >> k2 >> kk >> bb >> ms && k2 == key) {
+            if (ls >> k2 >> kk >> bb >> hh >> ms && k2 == key) {
                 opt->k = kk;
                 opt->block = bb;
+                opt->hops = hh;
                 if (best_ms) *best_ms = ms;
                 return PCH_OK;
             }
@@ -1349,30 +1445,35 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
     trial.out_on_device = 0;
     double best = 1e300;
     long long best_k = 0;
-    int best_b = 0;
+    int best_b = 0, best_h = 0;
     std::vector<long long> ks;
-    for (long long k = 4096; k <= std::max<long long>(4096, 4LL * m->dm.nf); k *= 4) ks.push_back(k);
-    const int blocks[3] = {128, 256, 512};
+    for (long long k = 24576; k <= std::max<long long>(24576, 8LL * m->dm.nf); k *= 4) ks.push_back(k);
+    const int blocks[2] = {128, 256};
+    const int hopss[4] = {1, 2, 4, 8};
     for (long long k : ks) {
         for (int b : blocks) {
-            trial.k = k;
-            trial.block = b;
-            double ms_sum = 0.0;
-            for (int rep = 0; rep < 2; ++rep) {   // first run warms the graph cache
-                pch_stats st{};
-                pch_status rc = solve_instances(&m, 1, &sd, 1, &trial, nullptr, kOutNone, &st);
-                if (rc != PCH_OK) return rc;
-                if (rep == 1) ms_sum = st.ms_total;
+            for (int hp : hopss) {
+                trial.k = k;
+                trial.block = b;
+                trial.hops = hp;
+                double ms_sum = 0.0;
+                for (int rep = 0; rep < 2; ++rep) {   // first run warms the graph cache
+                    pch_stats st{};
+                    pch_status rc = solve_instances(&m, 1, &sd, 1, &trial, nullptr, kOutNone, &st);
+                    if (rc != PCH_OK) return rc;
+                    if (rep == 1) ms_sum = st.ms_total;
+                }
+                if (ms_sum < best) { best = ms_sum; best_k = k; best_b = b; best_h = hp; }
             }
-            if (ms_sum < best) { best = ms_sum; best_k = k; best_b = b; }
         }
     }
     opt->k = best_k;
     opt->block = best_b;
+    opt->hops = best_h;
     if (best_ms) *best_ms = best;
     if (cache_path) {
         std::ofstream out(cache_path, std::ios::app);
-        out << key << " " << best_k << " " << best_b << " " << best << "\n";
+        out << key << " " << best_k << " " << best_b << " " << best_h << " " << best << "\n";
     }
     return PCH_OK;
 }

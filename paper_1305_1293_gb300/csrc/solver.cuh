@@ -21,13 +21,14 @@ struct SolveCfg {
     int unroll;
     int full_fan;
     int profile;
-    int pad;
+    int hops;
     const float* mlp;
 };
 
 enum { kOutHost = 0, kOutDevice = 1, kOutNone = 2 };
 
 long long default_k();
+int default_hops();
 const float* mlp_device_params();
 
 pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* srcs, int n_src,

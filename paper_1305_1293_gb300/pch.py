@@ -38,14 +38,15 @@ class Source(ctypes.Structure):
 class Options(ctypes.Structure):
     _fields_ = [("control", ctypes.c_int32), ("loop", ctypes.c_int32), ("k", ctypes.c_int64),
                 ("max_iters", ctypes.c_int64), ("stream", ctypes.c_void_p), ("out_on_device", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("flags", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("flags", ctypes.c_int32), ("hops", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int64), ("windows_created", ctypes.c_int64),
                 ("windows_propagated", ctypes.c_int64), ("peak_pending", ctypes.c_int64),
                 ("ms_total", ctypes.c_double), ("ms_setup", ctypes.c_double), ("bytes_workspace", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 6)]
+                ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 6), ("fans", ctypes.c_int64),
+                ("fan_windows", ctypes.c_int64), ("fan_candidates", ctypes.c_int64), ("windows_chained", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "ms_phase"}
@@ -107,11 +108,11 @@ def _stream_of(stream):
 
 
 def make_options(control=CONTROL_PLAIN, loop=LOOP_GRAPH, k=0, max_iters=0, stream=None, out_on_device=False,
-                 block=0, flags=0) -> Options:
+                 block=0, flags=0, hops=0) -> Options:
     o = Options()
     o.control, o.loop, o.k, o.max_iters = control, loop, k, max_iters
     o.stream = _stream_of(stream)
-    o.out_on_device, o.block, o.flags = int(bool(out_on_device)), block, flags
+    o.out_on_device, o.block, o.flags, o.hops = int(bool(out_on_device)), block, flags, hops
     return o
 
 
@@ -234,10 +235,20 @@ def measure_fp64_peak() -> float:
 
 
 def autotune(mesh: Mesh, source: int, cache_path: str | None = None, **opts):
-    """Fastest (k, block) for this mesh and source; returns (k, block, ms)."""
+    """Fastest (k, block, hops) for this mesh and source; returns a dict with the time."""
     src = make_source(source)
     o = make_options(**opts)
     ms = ctypes.c_double()
     _check(lib.pch_autotune(mesh.handle, ctypes.byref(src), ctypes.byref(o),
                             cache_path.encode() if cache_path else None, ctypes.byref(ms)))
-    return int(o.k), int(o.block), ms.value
+    return {"k": int(o.k), "block": int(o.block), "hops": int(o.hops), "ms": ms.value}
+
+
+def load_controller(path: str | None = None) -> bool:
+    """Install trained controller weights (default: controller_weights.npy next to this
+    module).  Returns False if the file does not exist."""
+    path = path or os.path.join(_HERE, "controller_weights.npy")
+    if not os.path.exists(path):
+        return False
+    mlp_set_weights(np.load(path))
+    return True

@@ -111,14 +111,17 @@ def test_parity_icosphere_full(pch, oracle_lib):
         assert st["iterations"] > 1
 
 
-@pytest.mark.parametrize("k", [1, 7, 256, 4096, 1 << 22])
-def test_result_independent_of_k(pch, oracle_lib, k):
+@pytest.mark.parametrize("k,hops", [(1, 1), (7, 1), (256, 1), (4096, 1), (1 << 22, 1), (1, 8), (64, 2),
+                                    (4096, 4), (1 << 22, 16)])
+def test_result_independent_of_k_and_hops(pch, oracle_lib, k, hops):
     """Section 4.3 / Remark 2: any selection order gives the exact field."""
     m = mg.terrain(24, 20, seed=31)
     s = mg.terrain_center(24, 20)
     ref, _ = oracle_lib.geodesic(m.vertices, m.faces, s)
-    got, _ = gpu_solve(pch, m, s, k=k, max_iters=1 << 22)
+    got, st = gpu_solve(pch, m, s, k=k, hops=hops, max_iters=1 << 22)
     assert max_rel(got, ref) < TOL
+    if hops == 1:
+        assert st["windows_chained"] == 0
 
 
 @pytest.mark.parametrize("flags", ["NO_TRIM", "FULL_FAN", "NO_TRIM|FULL_FAN"])
