@@ -165,6 +165,18 @@ pch_status pch_mlp_forward(const float* params_dev, const float* x_dev, int32_t 
  * grad_dev gets num_params floats, loss_dev one float.  Deterministic reduction. */
 pch_status pch_mlp_backward(const float* params_dev, const float* x_dev, const float* target_dev,
                             int32_t n, float* grad_dev, float* loss_dev, void* stream);
+/* Same result as pch_mlp_backward, without allocating: for callers that cannot call
+ * cudaMalloc, such as a host application whose own memory manager owns all device
+ * memory, or a training loop that must not stall on or fail an allocation mid-run.
+ * There is no counterpart in the paper.  Its scratch is one fixed device array of the
+ * library (6.3 MB, held on every GPU that loads the library until exit), so n is
+ * limited to 4096 samples; a larger n returns PCH_ERR_CAPACITY and computes nothing.
+ * The first call on a device looks the array up for that device; make that first call
+ * before any stream capture.  All calls share the array: calls whose work overlaps on
+ * the GPU (other threads, other streams) race and must be serialised by the caller.
+ * Nothing in the array needs clearing between calls. */
+pch_status pch_mlp_backward_noalloc(const float* params_dev, const float* x_dev, const float* target_dev,
+                                    int32_t n, float* grad_dev, float* loss_dev, void* stream);
 /* One Adam step in place (device pointers; m_dev, v_dev: moment buffers; t >= 1). */
 pch_status pch_mlp_adam(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev,
                         int32_t t, float lr, void* stream);

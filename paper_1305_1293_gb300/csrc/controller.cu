@@ -2,6 +2,7 @@
 // and the FP64 peak microbenchmark.  The network and its role are described in
 // controller.cuh; none of this has a counterpart in the paper, which fixes k by hand
 // (Section 5.2).
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <vector>
@@ -263,5 +264,58 @@ extern "C" pch_status pch_measure_fp64_peak(double* tflops) {
     PCH_CUDA(e);
     double flops = 2.0 * 8.0 * (double)iters * blocks * threads;
     *tflops = flops / (ms * 1e-3) / 1e12;
+    return PCH_OK;
+}
+
+// ---------------------------------------------------------------- allocation-free backward
+// Scratch of pch_mlp_backward_noalloc, in a file-scope device array instead of a
+// cudaMallocAsync buffer: per-sample activations and deltas (3 x 64 floats each), the
+// outputs and their errors, for at most kNoAllocMaxSamples samples (6.3 MB).  Every
+// GPU that loads the library holds this array until the process exits.
+namespace pch {
+constexpr int kNoAllocMaxSamples = 4096;
+constexpr size_t kNoAllocActFloats = (size_t)kNoAllocMaxSamples * 3 * kHidden;
+constexpr size_t kNoAllocFloats = 2 * kNoAllocActFloats + 2 * (size_t)kNoAllocMaxSamples;
+static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
+constexpr int kNoAllocMaxDevices = 64;
+// Host side: the array's device address, resolved once per device.  The symbol itself
+// is only a host-side stand-in and must never be handed to a kernel.
+static std::atomic<float*> g_noalloc_addr[kNoAllocMaxDevices];
+}  // namespace pch
+
+extern "C" pch_status pch_mlp_backward_noalloc(const float* params_dev, const float* x_dev, const float* target_dev,
+                                               int32_t n, float* grad_dev, float* loss_dev, void* stream) {
+    clear_error();
+    if (!params_dev || !x_dev || !target_dev || !grad_dev || !loss_dev || n <= 0)
+        return set_error(PCH_ERR_INVALID_ARG, "bad arguments");
+    if (n > kNoAllocMaxSamples)
+        return set_error(PCH_ERR_CAPACITY, "pch_mlp_backward_noalloc takes at most %d samples (got %d)",
+                         kNoAllocMaxSamples, n);
+    int dev = 0;
+    PCH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(PCH_ERR_INVALID_ARG, "device id %d out of range", dev);
+    float* scratch = g_noalloc_addr[dev].load();
+    if (!scratch) {
+        // first call on this device (the device is current): look the array up
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr)
+            return set_error(PCH_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                             cudaGetErrorString(e));
+        scratch = static_cast<float*>(p);
+        g_noalloc_addr[dev].store(scratch);
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    float* act = scratch;
+    float* dlt = act + kNoAllocActFloats;
+    float* y = dlt + kNoAllocActFloats;
+    float* dy = y + kNoAllocMaxSamples;
+    // every scratch element read below is written first by the same call: nothing to clear
+    int g = std::min(n, 65535);
+    k_mlp_fwd<<<g, kHidden, 0, s>>>(params_dev, x_dev, n, y, act);
+    k_mlp_bwd<<<g, kHidden, 0, s>>>(params_dev, act, y, target_dev, n, dlt, dy);
+    k_mlp_grad<<<(kMlpParams + 255) / 256, 256, 0, s>>>(x_dev, act, dlt, dy, n, grad_dev);
+    k_mlp_loss<<<1, 256, 0, s>>>(y, target_dev, n, loss_dev);
+    PCH_CUDA(cudaGetLastError());
     return PCH_OK;
 }

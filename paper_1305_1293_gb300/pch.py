@@ -72,6 +72,7 @@ def _load():
         "pch_mlp_set_weights": (I32, [P, I32]),
         "pch_mlp_forward": (I32, [P, P, I32, P, P]),
         "pch_mlp_backward": (I32, [P, P, P, I32, P, P, P]),
+        "pch_mlp_backward_noalloc": (I32, [P, P, P, I32, P, P, P]),
         "pch_mlp_adam": (I32, [P, P, P, P, I32, ctypes.c_float, P]),
         "pch_trace_fetch": (I32, [P, I32, P, P, P]),
         "pch_measure_fp64_peak": (I32, [P]),
@@ -212,6 +213,12 @@ def mlp_forward(params_dev, x_dev, y_dev, stream=None):
 def mlp_backward(params_dev, x_dev, target_dev, grad_dev, loss_dev, stream=None):
     _check(lib.pch_mlp_backward(_ptr(params_dev), _ptr(x_dev), _ptr(target_dev), int(x_dev.shape[0]),
                                 _ptr(grad_dev), _ptr(loss_dev), _stream_of(stream)))
+
+
+def mlp_backward_noalloc(params_dev, x_dev, target_dev, grad_dev, loss_dev, stream=None):
+    """pch_mlp_backward without any allocation (at most 4096 samples)."""
+    _check(lib.pch_mlp_backward_noalloc(_ptr(params_dev), _ptr(x_dev), _ptr(target_dev), int(x_dev.shape[0]),
+                                        _ptr(grad_dev), _ptr(loss_dev), _stream_of(stream)))
 
 
 def mlp_adam(params_dev, grad_dev, m_dev, v_dev, t: int, lr: float, stream=None):
