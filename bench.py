@@ -30,9 +30,6 @@ UNIT = "windows/s"
 WORKLOAD = "terrain512: 512x512 height-field grid (263,169 V, 524,288 F), 8 sines + N(0,0.01^2), random diagonals, source = centre vertex, fp64"
 NEAR_SAMPLE = 2500        # oracle sample: stop once the 2,500 nearest vertices are final
 FP64_PEAK_DERIVED = 152 * 4 * 2.07e9 / 1e12   # SMs x FP64 flops/clk/SM x max clock (TFLOP/s)
-# FP64 operations of one propagated window on the common path of k_propagate (counted
-# from the kernel source: 1 per add/sub/mul/div/sqrt/compare, 2 per fused multiply-add).
-FP64_OPS_PER_WINDOW = 180
 
 
 def _dist_env():
@@ -130,10 +127,10 @@ def run_reference(args):
 def run_gpu(args):
     import torch
     ws, rank, local = _dist_env()
+    torch.cuda.set_device(local)
     if ws > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     import __graft_entry__
     if rank == 0 or ws == 1:
         __graft_entry__.build()
@@ -201,7 +198,7 @@ def run_gpu(args):
     prop_launches = pst["iterations"]
     # the paper's own setting on the same GPU and kernels: k = 24 * 2^10, one hop
     _, paper_st = pch.solve(mesh, s, stats=True, k=24576, hops=1)
-    achieved_tf = FP64_OPS_PER_WINDOW * pst["windows_propagated"] / (prop_ms / 1e3) / 1e12
+    achieved_tf = pst["prop_fp64_ops"] / (prop_ms / 1e3) / 1e12
     fp64_meas = pch.measure_fp64_peak()
 
     # end to end through the C ABI with host buffers (mesh upload + solve + download)
@@ -246,9 +243,11 @@ def run_gpu(args):
             "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": achieved_tf,
                          "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_DERIVED,
                          "traffic": None, "fp64_microbench_tflops": fp64_meas,
-                         "ops_per_window": FP64_OPS_PER_WINDOW, "launches": prop_launches,
+                         "fp64_ops_per_launch": pst["prop_fp64_ops"] / max(1, prop_launches),
+                         "fp64_ops_per_window": pst["prop_fp64_ops"] / max(1, pst["windows_propagated"]),
+                         "launches": prop_launches,
                          "avg_launch_us": 1e3 * prop_ms / max(1, prop_launches),
-                         "phase_ms": ph},
+                         "phase_ms": ph, "memory_phases": phase_rooflines(pst, pst["sort_passes"])},
             "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": f"sequential oracle on the same terrain, stopped once the {NEAR_SAMPLE} "
                                        f"nearest vertices are final ({cpu_w} windows, {cpu_dt:.1f} s)"},
@@ -266,6 +265,102 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+HBM_PEAK_GBS = 6699.8   # measured STREAM-style copy bandwidth of a GB300 (MEASURED_PEAKS.json hbm_gbs)
+
+
+def phase_rooflines(pst, passes):
+    """Achieved FP64 rate of k_propagate and HBM rates of the memory-bound phases from the
+    algorithmic work counted in one profiled solve (bytes per window as in the comments below)."""
+    ph = pst["ms_phase"]
+    out = {"propagate_fp64_tflops": pst["prop_fp64_ops"] / max(ph["propagate"], 1e-9) / 1e9}
+    sel_bytes = 128 * pst["windows_scanned"]                        # 60 B in + 60 B out + 8 B gather
+    sort_bytes = pst["windows_sorted"] * (8 + 20 * passes)          # pass 0 reads he/inst; 4+8+8 B a pass
+    app_bytes = 240 * pst["windows_sorted"]                         # key/index 8, window 60, record 96, g 16, out 60
+    for name, b, ms in (("select", sel_bytes, ph["select"]), ("sort", sort_bytes, ph["sort"]),
+                        ("append", app_bytes, ph["append"])):
+        gbs = b / max(ms, 1e-9) / 1e6
+        out[name + "_gbs"] = gbs
+        out[name + "_hbm_frac"] = gbs / HBM_PEAK_GBS
+    out["propagate_fp64_frac"] = out["propagate_fp64_tflops"] / FP64_PEAK_DERIVED
+    return out
+
+
+def run_workload(args):
+    """Per-workload report line (not the default bench): plain with the paper's k, plain
+    with a tuned fixed k, the learned controller, and for multi-instance workloads one
+    batched launch against sequential solves; parity sampled against the oracle."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import oracle
+    from paper_1305_1293_gb300 import meshgen as mg, pch
+    pch.load_controller()
+    meshes, srcs = mg.workload(args.workload, "full")
+    handles = [pch.Mesh(m.vertices, m.faces) for m in meshes]
+    inst = [(i, int(s)) for i, ss in enumerate(srcs) for s in ss]
+    if args.workload == "torus":
+        inst = inst[:4]
+    hmesh = [handles[i] for i, _ in inst]
+    hsrc = [s for _, s in inst]
+
+    def seq(**kw):
+        t = w = 0
+        outs = []
+        for h, s in zip(hmesh, hsrc):
+            pch.solve(h, s, **kw)                                  # warm the graph
+            d, st = pch.solve(h, s, stats=True, **kw)
+            t += st["ms_total"]
+            w += st["windows_propagated"]
+            outs.append(d)
+        return t, w, outs
+
+    def batched(**kw):
+        pch.solve_batch(hmesh, hsrc, **kw)
+        outs, st = pch.solve_batch(hmesh, hsrc, stats=True, **kw)
+        return st["ms_total"], st["windows_propagated"], outs, st
+
+    res = {}
+    single = len(inst) == 1
+    big = sum(m.nf for m in meshes) * len(inst) / len(meshes) > 3e7
+    if not big:
+        res["plain_paper_k24576_hops1"] = seq(k=24576, hops=1)[:2]
+    tuned = pch.autotune(handles[0], hsrc[0], cache_path=os.path.join(ROOT, "paper_1305_1293_gb300", "autotune_cache.txt"))
+    tk = {"k": tuned["k"], "block": tuned["block"], "hops": tuned["hops"]}
+    if not big:
+        res["plain_tuned"] = seq(**tk)[:2]
+        res["learned"] = seq(control=pch.CONTROL_LEARNED)[:2]
+    final = None
+    if not single:
+        t, w, outs, st = batched(control=pch.CONTROL_LEARNED, block=tk["block"], hops=tk["hops"])
+        res["batched_learned"] = (t, w)
+        t2, w2, outs2, st2 = batched(**tk)
+        res["batched_tuned"] = (t2, w2)
+        final = outs2 if t2 < t else outs
+    else:
+        final = seq(**tk)[2]
+    # parity on sampled vertices of every instance (oracle early stop), at most 8 instances
+    worst = 0.0
+    for (i, s), d in list(zip(inst, final))[:8]:
+        m = meshes[i]
+        near = np.argsort(d)[1:151].astype(np.int32)
+        ref, _ = oracle.geodesic(m.vertices, m.faces, s, targets=near)
+        worst = max(worst, float(np.max(np.abs(d[near] - ref[near]) / ref[near])))
+    # profiled run of the tuned configuration on the first instance (roofline)
+    _, pst = pch.solve(hmesh[0], hsrc[0], stats=True, flags=pch.FLAG_PROFILE, **tk)
+    roof = phase_rooflines(pst, pst["sort_passes"])
+    best_name = min(res, key=lambda k: res[k][0])
+    t, w = res[best_name]
+    line = {"workload": args.workload, "metric": METRIC, "value": w / (t / 1e3), "unit": UNIT,
+            "ms_per_step": t, "best_form": best_name, "instances": len(inst),
+            "faces_total": int(sum(meshes[i].nf for i, _ in inst)),
+            "forms_ms_windows": {k: [round(v[0], 2), int(v[1])] for k, v in res.items()},
+            "tuned": tk, "parity_max_rel_err_sampled": worst, "roofline_first_instance": roof}
+    print(json.dumps(line), flush=True)
+    for h in handles:
+        h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -274,11 +369,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--k", type=int, default=0, help="windows per iteration (0 = autotuned)")
     ap.add_argument("--hops", type=int, default=0, help="with --k: propagation hops (0 = library default)")
+    ap.add_argument("--workload", default="terrain",
+                    choices=["terrain", "icosphere", "torus", "batch", "multisrc", "large"],
+                    help="terrain = the benchmark line; others print a per-workload report line")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="iteration driver: CUDA graph with device-side termination, or host-driven (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload != "terrain":
+        run_workload(args)
     else:
         run_gpu(args)
 

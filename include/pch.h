@@ -110,6 +110,10 @@ typedef struct {
     int64_t fan_windows;          /* windows those fans created */
     int64_t fan_candidates;       /* distance events at pseudo-source vertices examined */
     int64_t windows_chained;      /* children propagated in the same iteration (hops > 1) */
+    int64_t prop_fp64_ops;        /* algorithmic FP64 operations of the propagation kernel */
+    int64_t windows_scanned;      /* pending windows read by the selection compaction */
+    int64_t windows_sorted;       /* new windows sorted by the organisation step */
+    int64_t sort_passes;          /* 8-bit radix passes per sort */
 } pch_stats;
 
 /* Build a mesh: host arrays `vertices` (n_vertices x 3 doubles, xyz) and `faces`
@@ -151,8 +155,8 @@ void pch_destroy(pch_mesh* m);
 const char* pch_last_error(void);
 
 /* ---- learned selection controller (build-only; no counterpart in the paper) -----------
- * A 3 x 64 hidden-layer fp32 MLP maps per-iteration frontier statistics to the next
- * selection threshold.  Weights are a flat fp32 array of pch_mlp_num_params() values
+ * A 3 x 64 hidden-layer fp32 MLP maps per-iteration frontier statistics to the number of
+ * windows the next selection takes (output log2(k) / 24, k in [2^8, 2^26]).  Weights are a flat fp32 array of pch_mlp_num_params() values
  * (layer by layer: W then b, W row-major [out][in]). */
 int32_t pch_mlp_num_features(void);
 int32_t pch_mlp_num_params(void);
@@ -180,9 +184,9 @@ pch_status pch_mlp_backward_noalloc(const float* params_dev, const float* x_dev,
 /* One Adam step in place (device pointers; m_dev, v_dev: moment buffers; t >= 1). */
 pch_status pch_mlp_adam(float* params_dev, const float* grad_dev, float* m_dev, float* v_dev,
                         int32_t t, float lr, void* stream);
-/* Per-iteration features and chosen thresholds of the last solve on this mesh's
- * workspace (the controller's training traces): up to max_rows rows of
- * num_features floats into features (host), selected fraction into chosen (host). */
+/* Per-iteration features and choices of the last solve on this mesh's workspace (the
+ * controller's training traces): up to max_rows rows of num_features floats into
+ * features (host), log2(k) / 24 of the k used into chosen (host). */
 pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float* chosen,
                            int32_t* n_rows);
 
@@ -197,6 +201,11 @@ pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_options* opt, co
                         double* best_ms);
 
 /* ---- measurement helpers ---------------------------------------------------------- */
+/* Accuracy check of the library's FP64 reciprocal and square root (Newton-Raphson from a
+ * single-precision estimate) against IEEE 1/x and sqrt(|x|) on n device doubles x_dev:
+ * max_ulp_host[0], [1] get the largest distance in units in the last place. */
+pch_status pch_selftest_math(const double* x_dev, int32_t n, unsigned long long* max_ulp_host);
+
 /* Sustained FP64 FMA rate of this GPU (TFLOP/s, 2 flops per FMA) from a
  * register-resident DFMA loop; the roofline denominator for the propagation kernel. */
 pch_status pch_measure_fp64_peak(double* tflops);

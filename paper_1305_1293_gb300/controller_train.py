@@ -6,10 +6,12 @@ Recipe (build-side; the paper fixes k by hand, Section 5.2):
      workload (``TRAIN_SEED``), one or two random sources each.
   2. Threshold sweep: solve each with the plain control at k in ``SWEEP_K`` and record
      every iteration's frontier features (PCH_FLAG_TRACE) and the solve time.
-  3. Labels: every recorded state (from every k) gets the selection the fastest k of
-     that mesh would have made there, y = log2(min(1, k_best / pending)).
-  4. Fit: 3 x 64 ReLU MLP, loss 0.5 mean (y_hat - y)^2, Adam, using the library's
-     pch_mlp_backward / pch_mlp_adam kernels (no autograd).
+  3. Labels: every recorded state (from every k) gets y = log2(k_best) / 24, the best k of
+     that mesh: the largest one within 3% of the fastest solve (the time-vs-k curve has a
+     cliff below a plateau; labels on the far side are robust to prediction error).
+  4. Fit: 3 x 64 ReLU MLP, loss 0.5 mean (y_hat - y)^2, Adam with a cosine learning-rate
+     decay, keeping the lowest-loss weights, using the library's pch_mlp_backward /
+     pch_mlp_adam kernels (no autograd).
 The weights are written to ``controller_weights.npy`` next to this file.
 """
 from __future__ import annotations
@@ -24,7 +26,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "controller_weights.npy")
 TRAIN_SEED = 0x7A1E5
-SWEEP_K = (4096, 16384, 65536, 262144, 1048576)
+SWEEP_K = (4096, 16384, 65536, 262144, 1048576, 4194304)
 
 
 def training_set():
@@ -35,11 +37,18 @@ def training_set():
         out += [mg.icosphere(4 + i % 2, 0.02, seed=s), mg.geodesic_sphere(40 + 30 * i, 0.02, seed=s),
                 mg.terrain(96 + 64 * i, 96 + 48 * i, seed=s), mg.torus(200 + 150 * i, 60 + 40 * i, seed=s),
                 mg.multi_octave_sphere(5 + i % 2, 0.05, seed=s)]
+    s = TRAIN_SEED + 10
+    out += [mg.terrain(320, 320, seed=s), mg.terrain(400, 360, seed=s + 1), mg.torus(700, 200, seed=s + 2),
+            mg.multi_octave_sphere(7, 0.05, seed=s + 3), mg.geodesic_sphere(120, 0.02, seed=s + 4),
+            mg.torus(900, 250, seed=s + 5), mg.geodesic_sphere(90, 0.05, seed=s + 6),
+            mg.torus(400, 130, jitter=0.2, seed=s + 7)]
     return out
 
 
 def sweep(pch, mesh_np, sources, ks=SWEEP_K):
     """Features, labels and per-k solve times of one training mesh."""
+    if mesh_np.nf > 100000:
+        ks = tuple(k for k in ks if k >= 16384)      # k = 4096 is far from best there, and slow
     mesh = pch.Mesh(mesh_np.vertices, mesh_np.faces)
     feats, labels, times = [], [], {}
     traces = {}
@@ -53,13 +62,12 @@ def sweep(pch, mesh_np, sources, ks=SWEEP_K):
             traces.setdefault(k, []).append(f)
         times[k] = t
     mesh.close()
-    k_best = min(times, key=times.get)
+    t_best = min(times.values())
+    k_best = max(k for k, t in times.items() if t <= 1.03 * t_best)
     for k, fl in traces.items():
         for f in fl:
-            pending = np.exp2(20.0 * f[:, 0].astype(np.float64)) - 1.0
-            y = np.log2(np.minimum(1.0, k_best / np.maximum(pending, 1.0)))
             feats.append(f)
-            labels.append(y.astype(np.float32))
+            labels.append(np.full(f.shape[0], math.log2(k_best) / 24.0, dtype=np.float32))
     return np.concatenate(feats), np.concatenate(labels), times, k_best
 
 
@@ -88,14 +96,21 @@ def fit(pch, X, y, epochs=3000, lr=3e-3, seed=1, log=None):
     xd = torch.from_numpy(np.ascontiguousarray(X, dtype=np.float32)).cuda()
     yd = torch.from_numpy(np.ascontiguousarray(y, dtype=np.float32)).cuda()
     losses = []
+    best = float("inf")
+    best_p = p.clone()
     for t in range(1, epochs + 1):
-        pch.mlp_backward(p, xd, yd, g, loss)
-        pch.mlp_adam(p, g, m, v, t, lr)
+        pch.mlp_backward(p, xd, yd, g, loss)          # loss of the current parameters
+        lt = float(loss.item())
+        if lt < best:
+            best = lt
+            best_p.copy_(p)
+        pch.mlp_adam(p, g, m, v, t, lr * 0.5 * (1.0 + math.cos(math.pi * t / epochs)))
         if t % 250 == 0 or t == 1:
-            losses.append((t, float(loss.item())))
+            losses.append((t, lt))
             if log:
-                log(f"epoch {t} loss {losses[-1][1]:.5f}")
-    return p.cpu().numpy(), losses
+                log(f"epoch {t} loss {lt:.6f} best {best:.6f}")
+    losses.append((epochs, best))
+    return best_p.cpu().numpy(), losses
 
 
 def main():
@@ -106,7 +121,7 @@ def main():
     t0 = time.time()
     Xs, ys = [], []
     for mesh in training_set():
-        srcs = mg.pick_sources(mesh, 2, TRAIN_SEED + mesh.nv)
+        srcs = mg.pick_sources(mesh, 2 if mesh.nf <= 100000 else 1, TRAIN_SEED + mesh.nv)
         X, y, times, kb = sweep(pch, mesh, srcs)
         print(f"{mesh.name:>18s} F={mesh.nf:8d} best k={kb:8d} " +
               " ".join(f"{k}:{t:.1f}ms" for k, t in times.items()), flush=True)

@@ -3,7 +3,7 @@
 // The paper controls each iteration with a fixed window count k (Section 4.2, Step 1;
 // the trade-off of Section 5.2, Fig. `fig:parameter`).  This controller replaces the
 // fixed k by a 3 x 64 hidden-layer fp32 MLP that maps the frontier statistics of one
-// instance to log2 of the fraction of its pending windows to select.  Any window order
+// instance to log2 of the number of windows to select, divided by 24.  Any window order
 // gives the same distances (Section 4.3, Remark 2), so the controller can change speed,
 // never results; a non-finite or out-of-range output falls back to the plain k.
 #pragma once

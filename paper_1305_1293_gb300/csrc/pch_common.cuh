@@ -120,6 +120,8 @@ struct Counters {
     int halt;               // set by k_finish when the loop must stop; every kernel no-ops
     unsigned long long created, propagated, filtered, trimmed, peak_pending;
     unsigned long long fans, fan_windows, fan_cand, chained;
+    unsigned long long examined, occupied, children;   // propagation path counts (FP64 op tally)
+    unsigned long long scanned, sorted;               // windows read by compaction / sorted
     int work_next;          // next work-list index handed to a propagation lane
     int pad2;
 };
@@ -138,7 +140,8 @@ struct Work {
     WinSoA arena;           // children of this iteration (unsorted)
     int pool_cap, sel_cap, arena_cap, req_cap;
     int2* req[2];           // fan candidates (inst, vertex)
-    double2* req_d[2];      // fan candidates (distance, incoming direction; NaN = all directions)
+    double4* req_d[2];      // fan candidates: distance, reference angle, incoming direction (dx, dy)
+                            // in the reference half-edge's frame (NaN = all directions)
     unsigned* sort_key[2];
     int* sort_val[2];
     int* sort_hist;         // radix histograms
@@ -156,6 +159,10 @@ struct Work {
 // Ordered u64 image of a nonnegative double (atomicMin-able, Section 4.2 Step 4).
 __device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
 __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlong_as_double((long long)b); }
-__device__ __forceinline__ bool dominated(double lhs, double rhs) { return lhs > rhs * (1.0 + kDomRel); }
+// lhs > rhs (1 + kDomRel) for nonnegative lhs, rhs, decided on the ordered bit images so
+// it costs no FP64 instruction: within a binade 9008 units in the last place are between
+// 1e-12 and 2e-12 relative, so the test never removes a window the relative margin keeps.
+constexpr unsigned long long kDomUlps = 9008;
+__device__ __forceinline__ bool dominated(double lhs, double rhs) { return dbits(lhs) > dbits(rhs) + kDomUlps; }
 
 }  // namespace pch

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <vector>
 
+#include "fastmath.cuh"
 #include "pch_host.h"
 #include "radix.cuh"
 #include "solver.cuh"
@@ -90,12 +91,15 @@ __device__ __forceinline__ bool vertex_event(const Inst& I, unsigned vf, double 
     return false;
 }
 
-__device__ __forceinline__ void push_fan(int2* req, double2* req_d, int* n, int cap, int* err, int inst, unsigned v,
-                                         double D, double phi) {
+// A fan candidate carries the incoming ray as a direction (dx, dy) in the frame of a
+// reference half-edge leaving v whose angular position is `base`; the fan kernel turns
+// it into an angle (atan2) only for candidates that still hold the vertex's distance.
+__device__ __forceinline__ void push_fan(int2* req, double4* req_d, int* n, int cap, int* err, int inst, unsigned v,
+                                         double D, double base, double dx, double dy) {
     int slot = atomicAdd(n, 1);
     if (slot < cap) {
         req[slot] = make_int2(inst, (int)v);
-        req_d[slot] = make_double2(D, phi);
+        req_d[slot] = make_double4(D, base, dx, dy);
     } else {
         atomicOr(err, kErrReqFull);
     }
@@ -198,7 +202,8 @@ __global__ void k_init_sources(Work w, const SrcDev* __restrict__ srcs, int n_sr
         if (s.kind == 0) {
             I.g[s.vertex] = 0ull;
             // the source's fan covers every direction
-            push_fan(w.req[0], w.req_d[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, (unsigned)s.vertex, 0.0, NAN);
+            push_fan(w.req[0], w.req_d[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, (unsigned)s.vertex, 0.0, 0.0,
+                     NAN, NAN);
         }
     }
 }
@@ -221,9 +226,8 @@ __global__ void k_init_face_sources(Work w, const SrcDev* __restrict__ srcs, int
             double gc = ldg_dist(I.g, R.v0 & ~kPseudoBit);
             if (vertex_event(I, R.v0, dstart, gc)) {
                 // incoming direction: from the corner towards the point, inside face(h)
-                double phi = wrap_angle(I, R.v0 & ~kPseudoBit, I.vphi[h] + atan2(y, x));
                 push_fan(w.req[0], w.req_d[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, R.v0 & ~kPseudoBit,
-                         dstart, phi);
+                         dstart, I.vphi[h], x, y);
             }
             if (R.twin < 0) continue;
             // window on twin(h) = (v1 -> v0): point at (L - x, -y), interval [0, L]
@@ -266,11 +270,9 @@ __global__ void k_tau(Work w, int control, const float* __restrict__ mlp) {
             long long k = c.k_target;
             if (learned) {
                 c.ctl_out = y;
-                // y = log2 of the fraction of pending windows to select; plain k otherwise
-                if (isfinite(y) && y <= 0.f && y >= -24.f) {
-                    long long kk = (long long)ceil(exp2((double)y) * np);
-                    k = kk < 1 ? 1 : kk;
-                }
+                // y = log2(windows to select) / 24; the plain k when the output is not
+                // finite or outside [2^8, 2^26]
+                if (isfinite(y) && y >= 8.f / 24.f && y <= 26.f / 24.f) k = (long long)exp2(24.0 * (double)y);
             }
             if (np == 0) {
                 tau = -INFINITY;
@@ -290,7 +292,7 @@ __global__ void k_tau(Work w, int control, const float* __restrict__ mlp) {
                 if (row < w.trace_cap) {
                     float* f = w.trace + (size_t)row * (kFeatures + 2);
                     for (int j = 0; j < kFeatures; ++j) f[j] = feat[j];
-                    f[kFeatures] = (float)log2(fmin(1.0, (double)k / (double)np));
+                    f[kFeatures] = (float)(log2((double)k) / 24.0);
                     f[kFeatures + 1] = (float)inst;
                 }
             }
@@ -347,6 +349,7 @@ __global__ void __launch_bounds__(256) k_compact(Work w) {
 struct ChildOut {
     int he;
     double A, B, px, py, key;
+    double IA, IB;          // |I A|, |I B| (reused when the child is propagated at once)
 };
 
 // Ray from I' through P' (child frame, both below the child's x axis) meets the axis at
@@ -354,7 +357,7 @@ struct ChildOut {
 __device__ __forceinline__ void ray_hit(double Ipx, double Ipy, double Ppx, double Ppy, double IP, double Lc,
                                         double& xh, double& IX) {
     double den = Ppy - Ipy;
-    double t = -Ipy / den;
+    double t = -Ipy * rcp_nr(den);
     xh = Ipx + t * (Ppx - Ipx);
     IX = t * IP;
     if (!(den > 0.0) || !(xh >= 0.0 && xh <= Lc)) {
@@ -379,11 +382,14 @@ __device__ __forceinline__ bool dominated_sq(double lhs, double g, double q) {
 
 // Algorithm 2 for one window: events, one angle one split, children with the Xin-Wang
 // filter.  Returns whether the window passed the filter; children in c0, c1 (nch).
-__device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, int2* req, double2* req_d, int inst,
+__device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, int2* req, double4* req_d, int inst,
                                                  int src, double d, int h, double A, double B, double px, double py,
-                                                 ChildOut& c0, ChildOut& c1, int& nch) {
+                                                 ChildOut& c0, ChildOut& c1, int& nch, int& occ_out, int& ncomp,
+                                                 double IA_in, double IB_in) {
     bool prop = false;
     nch = 0;
+    occ_out = 0;
+    ncomp = 0;
         {
         const Inst& I = w.inst[inst];
         const HERec R = I.rec[h];
@@ -393,7 +399,9 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
         double g2 = ldg_dist(I.g, R.v2 & ~kPseudoBit);
         const double py2 = py * py;
         const double ax = A - px, bx = B - px;
-        const double IA = sqrt(ax * ax + py2), IB = sqrt(bx * bx + py2);
+        // |IA|, |IB|: carried over from the parent when the window was chained
+        const double IA = IA_in >= 0.0 ? IA_in : sqrt_nr(ax * ax + py2);
+        const double IB = IB_in >= 0.0 ? IB_in : sqrt_nr(bx * bx + py2);
         // Xin-Wang endpoint tests against the current distances: the window is
         // useless if the path via v0 beats it at B, or the path via v1 at A.
         if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)) || stale_source(I, src, d))) {
@@ -402,21 +410,16 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
             // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
             if (A <= tol) {
                 double D0 = d + (A == 0.0 ? IA : sqrt(px * px + py2));
-                if (vertex_event(I, R.v0, D0, g0)) {
-                    // the ray arrives at v0 through the twin face: direction to I
-                    const unsigned v = R.v0 & ~kPseudoBit;
-                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D0,
-                             wrap_angle(I, v, I.vphi[h] + atan2(py, px)));
-                }
+                if (vertex_event(I, R.v0, D0, g0))   // the ray arrives at v0 from I (h's frame)
+                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v0 & ~kPseudoBit, D0,
+                             I.vphi[h], px, py);
             }
             if (B >= L - tol) {
                 double q = L - px;
                 double D1 = d + (B == L ? IB : sqrt(q * q + py2));
-                if (vertex_event(I, R.v1, D1, g1)) {
-                    const unsigned v = R.v1 & ~kPseudoBit;
-                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D1,
-                             wrap_angle(I, v, I.vphi[R.twin] + atan2(py, -q) + 3.14159265358979323846));
-                }
+                if (vertex_event(I, R.v1, D1, g1))   // at v1, in the frame of twin(h) = (v1 -> v0)
+                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v1 & ~kPseudoBit, D1,
+                             I.vphi[R.twin], q, -py);
             }
             // occupancy of v2: the ray I -> v2 crosses e at xs = px + num / den;
             // decided without the division (den > 0)
@@ -424,13 +427,14 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
             const double den = yc - py, num = (xc - px) * (-py);
             const bool before_A = num < (A - tol - px) * den;
             const bool occ = !before_A && num <= (B + tol - px) * den;
+            occ_out = occ;
             bool left, right;
             double Iv2 = 0.0, xcl = 0.0;
             if (occ) {
-                const double xs = px + num / den;
+                const double xs = px + num * rcp_nr(den);
                 xcl = fmin(fmax(xs, A), B);
                 const double dx = xc - px, dy = yc - py;
-                Iv2 = sqrt(dx * dx + dy * dy);
+                Iv2 = sqrt_nr(dx * dx + dy * dy);
                 const double D2 = d + Iv2;
                 // one angle one split (Fig. `fig:filter`(a)) against angle_split[h]
                 unsigned long long* ap = I.ang + h;
@@ -448,14 +452,12 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
                     if (!left && !right) left = right = true;
                 }
                 if (vertex_event(I, R.v2, D2, g2)) {
-                    // the ray arrives at v2 inside face(h): angle from v2->v0 towards I
-                    const unsigned v = R.v2 & ~kPseudoBit;
+                    // the ray arrives at v2 inside face(h); direction to I in the frame of
+                    // prev(h) = (v2 -> v0), whose axis is (-xc, -yc) / L2
                     const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
-                    double da = atan2(py - yc, px - xc) - atan2(-yc, -xc);
-                    if (da < 0.0) da += 2.0 * 3.14159265358979323846;
-                    da = fmin(da, I.hang[hp]);
-                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, v, D2,
-                             wrap_angle(I, v, I.vphi[hp] + da));
+                    const double ux = -xc * R.iL2, uy = -yc * R.iL2, ex = px - xc, ey = py - yc;
+                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v2 & ~kPseudoBit, D2,
+                             I.vphi[hp], ex * ux + ey * uy, ux * ey - uy * ex);
                 }
                 if (B - xcl <= kEpsTiny * L) right = false;
                 if (xcl - A <= kEpsTiny * L) left = false;
@@ -472,6 +474,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
             for (int j = 0; j < 2; ++j) {
                 if (!(j == 0 ? (right || left) : (right && left))) break;
                 const bool rt = j == 0 && right;
+                ++ncomp;
                 const double Lc = rt ? R.L1 : R.L2;
                 const double ox = rt ? xc : 0.0, oy = rt ? yc : 0.0;
                 const double ux = rt ? (L - xc) * R.iL1 : xc * R.iL2;
@@ -510,7 +513,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
                               dominated_sq(d + IAc, g1, Xx * Xx + Xy * Xy);
                 }
                 if (useless) continue;
-                const ChildOut co{rt ? R.tw1 : R.tw2, a, b, Ipx, Ipy, child_key(d, a, b, Ipx, Ipy, IAc, IBc)};
+                const ChildOut co{rt ? R.tw1 : R.tw2, a, b, Ipx, Ipy, child_key(d, a, b, Ipx, Ipy, IAc, IBc), IAc, IBc};
                 if (nch == 0) c0 = co;
                 else c1 = co;
                 ++nch;
@@ -533,11 +536,11 @@ __global__ void __launch_bounds__(256) k_propagate(Work w, int hops) {
     const int it = cnt->iter;
     const int n = min(cnt->n_sel, w.sel_cap);
     int2* req = w.req[it & 1];
-    double2* req_d = w.req_d[it & 1];
+    double4* req_d = w.req_d[it & 1];
     const int room = w.arena_cap / 2 - 2 * (int)(gridDim.x * blockDim.x);
     bool have = false, exhausted = false;
     int h = 0, inst = 0, src = -1, hop = 0;
-    double d = 0.0, A = 0.0, B = 0.0, px = 0.0, py = 0.0;
+    double d = 0.0, A = 0.0, B = 0.0, px = 0.0, py = 0.0, cIA = -1.0, cIB = -1.0;
     while (true) {
         const unsigned need = __ballot_sync(full, !have);
         if (need && !exhausted) {
@@ -550,6 +553,7 @@ __global__ void __launch_bounds__(256) k_propagate(Work w, int hops) {
                 if (idx < n) {
                     h = w.sel.he[idx]; inst = w.sel.inst[idx]; d = w.sel.d[idx]; src = w.sel.src[idx];
                     A = w.sel.A[idx]; B = w.sel.B[idx]; px = w.sel.px[idx]; py = w.sel.py[idx];
+                    cIA = cIB = -1.0;
                     have = true;
                     hop = 0;
                 }
@@ -557,9 +561,10 @@ __global__ void __launch_bounds__(256) k_propagate(Work w, int hops) {
         }
         if (!__any_sync(full, have)) break;
         ChildOut c0, c1;
-        int nch = 0;
+        int nch = 0, occ = 0, ncomp = 0;
         bool prop = false;
-        if (have) prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, c0, c1, nch);
+        if (have)
+            prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, c0, c1, nch, occ, ncomp, cIA, cIB);
         bool cont = have && nch > 0 && hop + 1 < hops && c0.key <= w.ctl[inst].tau &&
                     *(volatile int*)&cnt->n_child < room;
         const int nwrite = have ? (cont ? nch - 1 : nch) : 0;
@@ -570,6 +575,7 @@ __global__ void __launch_bounds__(256) k_propagate(Work w, int hops) {
                 else atomicOr(&cnt->error, kErrPoolFull);
             }
             h = c0.he; A = c0.A; B = c0.B; px = c0.px; py = c0.py;
+            cIA = c0.IA; cIB = c0.IB;
             ++hop;
         } else if (have) {
             if (nch > 0) {
@@ -585,6 +591,9 @@ __global__ void __launch_bounds__(256) k_propagate(Work w, int hops) {
         }
         warp_add_ull(&cnt->propagated, prop ? 1 : 0);
         warp_add_ull(&cnt->chained, cont ? 1 : 0);
+        warp_add_ull(&cnt->examined, have ? 1 : 0);
+        warp_add_ull(&cnt->occupied, occ);
+        warp_add_ull(&cnt->children, ncomp);
     }
 }
 
@@ -658,16 +667,17 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
     const int nreq = min(cnt->n_req, w.req_cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cnt->fan_cand, (unsigned long long)nreq);
     const int2* req = w.req[it & 1];
-    const double2* req_d = w.req_d[it & 1];
+    const double4* req_d = w.req_d[it & 1];
     int2* req_nx = w.req[(it + 1) & 1];
-    double2* req_d_nx = w.req_d[(it + 1) & 1];
+    double4* req_d_nx = w.req_d[(it + 1) & 1];
     const unsigned stamp_fan = (unsigned)it + 1u;
     const int warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
     for (int r = warp0; r < nreq; r += nwarps) {
         const int inst = req[r].x;
         const unsigned v = (unsigned)req[r].y;
-        const double D = req_d[r].x, phi = req_d[r].y;
+        const double4 rq = req_d[r];
+        const double D = rq.x;
         const Inst& I = w.inst[inst];
         int ok = 0;
         if (lane == 0) {
@@ -678,6 +688,8 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
         if (!__shfl_sync(full, ok, 0)) continue;
         const int s = I.vstart[v], e = I.vstart[v + 1];
         const double T = I.vtheta[v];
+        // incoming direction as an angle around v (NaN: the source, every direction)
+        const double phi = rq.z == rq.z ? wrap_angle(I, v, rq.y + atan2(rq.w, rq.z)) : rq.z;
         const Wedges W = make_wedges(I.vflag[v] & 1, T, phi, full_fan != 0);
         if (W.n == 0) continue;
         bool deferred = false;
@@ -708,7 +720,7 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                 if (win && sl < w.arena_cap) w.arena.he[sl] = -1;
                 if (lane == 0) {
                     atomicExch(I.stamp + v, 0u);
-                    push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, v, D, phi);
+                    push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, v, D, rq.y, rq.z, rq.w);
                 }
                 deferred = true;
                 continue;
@@ -721,12 +733,14 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                 // boundary edge: endpoint events for the covered endpoints
                 const unsigned a = Ro.v0 & ~kPseudoBit, b = Ro.v1 & ~kPseudoBit;
                 double ga = ldg_dist(I.g, a), gb = ldg_dist(I.g, b);
+                // incoming directions: at a towards v is the far side of o's corner; at b it
+                // is the direction of next(o) = (b -> v)
                 if (s0 <= 0.0 && vertex_event(I, Ro.v0, D + Ro.L2, ga))
                     push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, a, D + Ro.L2,
-                             wrap_angle(I, a, I.vphi[o] + I.hang[o]));
+                             I.vphi[o], Ro.xc, Ro.yc);
                 if (s1 >= Lo && vertex_event(I, Ro.v1, D + Ro.L1, gb))
                     push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, b, D + Ro.L1,
-                             wrap_angle(I, b, I.vphi[he_next(o)]));
+                             I.vphi[he_next(o)], 1.0, 0.0);
                 continue;
             }
             // window on twin(o) = (b -> a): I = v at (Lo - xc, -yc), interval [Lo - s1, Lo - s0]
@@ -816,6 +830,8 @@ __global__ void __launch_bounds__(256) k_append(Work w, const unsigned* __restri
 __global__ void k_finish(Work w, cudaGraphConditionalHandle handle, int use_cond, long long max_iters) {
     Counters* c = w.cnt;
     if (!c->halt) {
+        c->scanned += (unsigned long long)min(c->n_pending, w.pool_cap);
+        c->sorted += (unsigned long long)min(c->n_child, w.arena_cap);
         int np = c->n_rest + c->n_app;
         const float ratio = c->n_sel > 0 ? (float)c->n_app / (float)c->n_sel : 0.f;
         for (int i = 0; i < w.n_inst; ++i) w.ctl[i].last_ratio = ratio;
@@ -971,7 +987,7 @@ static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap) {
             cudaMemcpy(nw.pool[p].key, w.pool[p].key, n * 8, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.pool[p].src, w.pool[p].src, n * 4, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.req[p], w.req[p], sizeof(int2) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
-            cudaMemcpy(nw.req_d[p], w.req_d[p], sizeof(double2) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.req_d[p], w.req_d[p], sizeof(double4) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
         }
         e = cudaDeviceSynchronize();
         if (e) { fresh.release(); return set_error(PCH_ERR_CUDA, "pool growth copy: %s", cudaGetErrorString(e)); }
@@ -1196,6 +1212,15 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         stats->fan_windows = (int64_t)c.fan_windows;
         stats->fan_candidates = (int64_t)c.fan_cand;
         stats->windows_chained = (int64_t)c.chained;
+        stats->windows_scanned = (int64_t)c.scanned;
+        stats->windows_sorted = (int64_t)c.sorted;
+        stats->sort_passes = (cfg.key_bits + kRsDigitBits - 1) / kRsDigitBits;
+        // algorithmic FP64 operations of k_propagate (add, sub, mul, div, sqrt = 1; fma = 2),
+        // counted per code path of propagate_window: filter 17 (11 for a chained window,
+        // whose |IA|, |IB| come from its parent), passed window +11, occupied v2 +20,
+        // each child computed +50 (30.5 plus 13 per ray intersected)
+        stats->prop_fp64_ops = (int64_t)(17ull * c.examined + 11ull * c.propagated + 20ull * c.occupied +
+                                         50ull * c.children) - (int64_t)(6ull * c.chained);
         for (int p = 0; p < 6; ++p) stats->ms_phase[p] = phase_ms[p];
     }
     return PCH_OK;
@@ -1475,5 +1500,34 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
         std::ofstream out(cache_path, std::ios::app);
         out << key << " " << best_k << " " << best_b << " " << best_h << " " << best << "\n";
     }
+    return PCH_OK;
+}
+
+// ---------------------------------------------------------------- math self-test
+__global__ void k_selftest_math(const double* __restrict__ x, int n, unsigned long long* maxulp) {
+    unsigned long long mr = 0, ms = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const double v = x[i];
+        const long long a = __double_as_longlong(rcp_nr(v)), b = __double_as_longlong(1.0 / v);
+        const long long c = __double_as_longlong(sqrt_nr(fabs(v))), d = __double_as_longlong(sqrt(fabs(v)));
+        unsigned long long ur = (unsigned long long)(a > b ? a - b : b - a);
+        unsigned long long us = (unsigned long long)(c > d ? c - d : d - c);
+        mr = ur > mr ? ur : mr;
+        ms = us > ms ? us : ms;
+    }
+    atomicMax(maxulp, mr);
+    atomicMax(maxulp + 1, ms);
+}
+
+extern "C" pch_status pch_selftest_math(const double* x_dev, int32_t n, unsigned long long* max_ulp_host) {
+    clear_error();
+    if (!x_dev || n <= 0 || !max_ulp_host) return set_error(PCH_ERR_INVALID_ARG, "bad arguments");
+    unsigned long long* d = nullptr;
+    PCH_CUDA(cudaMalloc(&d, 2 * sizeof(unsigned long long)));
+    cudaMemset(d, 0, 2 * sizeof(unsigned long long));
+    k_selftest_math<<<grid_for(2), 256>>>(x_dev, n, d);
+    cudaError_t e = cudaMemcpy(max_ulp_host, d, 2 * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    PCH_CUDA(e);
     return PCH_OK;
 }

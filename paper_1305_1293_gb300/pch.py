@@ -46,7 +46,9 @@ class Stats(ctypes.Structure):
                 ("windows_propagated", ctypes.c_int64), ("peak_pending", ctypes.c_int64),
                 ("ms_total", ctypes.c_double), ("ms_setup", ctypes.c_double), ("bytes_workspace", ctypes.c_int64),
                 ("kernel_launches", ctypes.c_int64), ("ms_phase", ctypes.c_double * 6), ("fans", ctypes.c_int64),
-                ("fan_windows", ctypes.c_int64), ("fan_candidates", ctypes.c_int64), ("windows_chained", ctypes.c_int64)]
+                ("fan_windows", ctypes.c_int64), ("fan_candidates", ctypes.c_int64), ("windows_chained", ctypes.c_int64),
+                ("prop_fp64_ops", ctypes.c_int64), ("windows_scanned", ctypes.c_int64),
+                ("windows_sorted", ctypes.c_int64), ("sort_passes", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "ms_phase"}
@@ -77,6 +79,7 @@ def _load():
         "pch_trace_fetch": (I32, [P, I32, P, P, P]),
         "pch_measure_fp64_peak": (I32, [P]),
         "pch_autotune": (I32, [P, P, P, ctypes.c_char_p, P]),
+        "pch_selftest_math": (I32, [P, I32, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -259,3 +262,10 @@ def load_controller(path: str | None = None) -> bool:
         return False
     mlp_set_weights(np.load(path))
     return True
+
+
+def selftest_math(x_dev):
+    """Largest ulp distance of the library's reciprocal and square root from IEEE."""
+    out = (ctypes.c_ulonglong * 2)()
+    _check(lib.pch_selftest_math(_ptr(x_dev), int(x_dev.shape[0]), out))
+    return int(out[0]), int(out[1])

@@ -119,3 +119,34 @@ def test_gpu_adam_matches_cpu(gpu):
         pc, mc, vc = mo.adam_step(pc, g.astype(np.float64), mc, vc, t, 1e-3)
     torch.cuda.synchronize()
     assert np.max(np.abs(pd.cpu().numpy() - pc)) < 1e-6
+
+
+@pytest.mark.gpu
+def test_trained_controller_gain_and_exactness(gpu, oracle_lib):
+    """What the trained network gains over the fixed-k method on a held-out jittered
+    torus (seeds disjoint from training), with the distances unchanged: any selection
+    order gives the exact field (Section 4.3, Remark 2)."""
+    torch, pch = gpu
+    from paper_1305_1293_gb300 import meshgen as mg
+    if not pch.load_controller():
+        pytest.skip("no trained weights (run paper_1305_1293_gb300.controller_train on a GPU)")
+    m = mg.torus(600, 200, seed=mg.SEED_BASE + 77)
+    srcs = mg.pick_sources(m, 2, mg.SEED_BASE + 78)
+    mesh = pch.Mesh(m.vertices, m.faces)
+    t_plain = t_learned = 0.0
+    for s in srcs:
+        s = int(s)
+        pch.solve(mesh, s, k=24576, hops=1)                       # warm both graphs
+        pch.solve(mesh, s, control=pch.CONTROL_LEARNED)
+        plain, sp = pch.solve(mesh, s, k=24576, hops=1, stats=True)   # the paper's fixed k
+        learned, sl = pch.solve(mesh, s, control=pch.CONTROL_LEARNED, stats=True)
+        t_plain += sp["ms_total"]
+        t_learned += sl["ms_total"]
+        assert np.max(np.abs(learned - plain) / np.maximum(plain, 1e-300)) < 1e-9
+        near = np.argsort(learned)[1:301].astype(np.int32)
+        ref, _ = oracle_lib.geodesic(m.vertices, m.faces, s, targets=near)
+        assert np.max(np.abs(learned[near] - ref[near]) / ref[near]) < 1e-9
+    mesh.close()
+    print(f"torus 600x200: plain k=24576 {t_plain:.1f} ms, learned {t_learned:.1f} ms, "
+          f"gain {t_plain / t_learned:.2f}x")
+    assert t_learned < t_plain
