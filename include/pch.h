@@ -114,6 +114,9 @@ typedef struct {
     int64_t windows_scanned;      /* pending windows read by the selection compaction */
     int64_t windows_sorted;       /* new windows sorted by the organisation step */
     int64_t sort_passes;          /* 8-bit radix passes per sort */
+    int64_t windows_examined;     /* windows the propagation kernel tested (selected + chained) */
+    int64_t windows_occupied;     /* of those, windows whose rays reach the opposite vertex */
+    int64_t children_computed;    /* child windows whose geometry was computed (before the filter) */
 } pch_stats;
 
 /* Build a mesh: host arrays `vertices` (n_vertices x 3 doubles, xyz) and `faces`
@@ -193,7 +196,7 @@ pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float
 /* ---- autotuner (build-only) ------------------------------------------------------------
  * Times full solves of `src` on `m` over a grid of windows-per-iteration k (24576 times
  * powers of 4, up to 8x the face count), propagation block sizes (128, 256) and hops
- * (1, 2, 4, 8), and writes the fastest into opt->k, opt->block and opt->hops (the other
+ * (2, 4, 8, 16, 32), and writes the fastest into opt->k, opt->block and opt->hops (the other
  * fields of *opt are kept and used for every trial).  If cache_path is not NULL the result is looked up first
  * in, and then appended to, that text file, keyed by GPU name and mesh size, so a
  * second call does no timing.  Errors: as pch_solve. */

@@ -35,6 +35,15 @@ int default_hops() {
     return 4;
 }
 
+int default_prop_blocks_per_sm() {
+    const char* e = std::getenv("PCH_PROP_BLOCKS_PER_SM");
+    if (e) {
+        int v = std::atoi(e);
+        if (v > 0 && v <= 32) return v;
+    }
+    return 4;
+}
+
 // ---------------------------------------------------------------- training kernels
 // One block of kHidden threads per sample.  act: [n][3][kHidden] post-ReLU activations.
 __global__ void __launch_bounds__(kHidden) k_mlp_fwd(const float* __restrict__ p, const float* __restrict__ x, int n,

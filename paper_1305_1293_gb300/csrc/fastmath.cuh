@@ -1,9 +1,12 @@
 // FP64 reciprocal and square root by Newton-Raphson iteration from the hardware's
 // single-precision estimates (PTX rcp.approx.ftz.f32 / rsqrt.approx.ftz.f32, relative
-// error about 2^-23).  Each step roughly doubles the correct bits (23 -> 46 -> 92), so two
-// steps reach the limit of FP64 rounding; results are within a few ulp of the IEEE
-// operations (checked by pch_selftest_math).  Inputs outside [1e-30, 1e30] (where the
-// single-precision seed would underflow or overflow) use the IEEE operations instead.
+// error about 2^-23).  The FP64 unit is the scarce resource of the propagation kernel, so
+// the range guard and the double <-> float conversions around the estimate are done on
+// the integer pipe: the seed is taken from x with its mantissa truncated to 20 bits
+// (relative error <= 2^-20, so seeds are good to about 2^-20), and each Newton step
+// roughly doubles the correct bits (20 -> 40 -> 80).  Results are within a few ulp of the
+// IEEE operations (checked by pch_selftest_math).  Inputs outside [2^-99, 2^99) (where a
+// single-precision seed could leave the normal range) use the IEEE operations instead.
 #pragma once
 #include <cuda_runtime.h>
 
@@ -21,27 +24,53 @@ __device__ __forceinline__ float rsqrt_approx_f32(float x) {
     return r;
 }
 
+// 2^-99 <= |x| < 2^99, from the biased exponent field.
+__device__ __forceinline__ bool nr_range(double x) {
+    const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
+    return e - (1023u - 99u) < 198u;
+}
+// 2^-99 <= x < 2^99 (the sign bit lands above the exponent field and fails the test).
+__device__ __forceinline__ bool nr_range_pos(double x) {
+    const unsigned e = (unsigned)__double2hiint(x) >> 20;
+    return e - (1023u - 99u) < 198u;
+}
+
+// x in the guarded range as a float: exponent rebiased (1023 -> 127), mantissa cut to
+// its top 20 bits.
+__device__ __forceinline__ float narrow_seed(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x);
+    return __uint_as_float((hi & 0x80000000u) | (((hi & 0x7fffffffu) - (896u << 20)) << 3));
+}
+
+// A normal float as the exactly equal double.
+__device__ __forceinline__ double widen_normal(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned hi = (b & 0x80000000u) | (((b & 0x7fffffffu) >> 3) + (896u << 20));
+    return __hiloint2double((int)hi, (int)(b << 29));
+}
+
 // 1 / x: r <- r + r (1 - x r), twice.
 __device__ __forceinline__ double rcp_nr(double x) {
-    const double ax = fabs(x);
-    if (!(ax > 1e-30 && ax < 1e30)) return 1.0 / x;
-    double r = (double)rcp_approx_f32((float)x);
+    if (!nr_range(x)) return 1.0 / x;
+    double r = widen_normal(rcp_approx_f32(narrow_seed(x)));
     double e = fma(-x, r, 1.0);
     r = fma(r, e, r);
     e = fma(-x, r, 1.0);
     return fma(r, e, r);
 }
 
-// sqrt(x) for x > 0: y ~ 1/sqrt(x) refined by y <- y (3/2 - x y^2 / 2) twice, then
-// s = x y and one correction s + (x - s^2) y / 2.
+// sqrt(x), coupled iteration on g ~ sqrt(x) and h ~ 1 / (2 sqrt(x)) from the
+// seed y ~ 1/sqrt(x): g = x y, h = y / 2, r = 1/2 - g h, g += g r, h += h r (both now
+// good to about 2^-40), then one Newton correction g + (x - g^2) h.
 __device__ __forceinline__ double sqrt_nr(double x) {
-    if (!(x > 1e-30 && x < 1e30)) return sqrt(x);
-    double y = (double)rsqrt_approx_f32((float)x);
-    const double h = 0.5 * x;
-    y = y * fma(-h * y, y, 1.5);
-    y = y * fma(-h * y, y, 1.5);
-    const double s = x * y;
-    return fma(fma(-s, s, x), 0.5 * y, s);
+    if (!nr_range_pos(x)) return sqrt(x);
+    const float y = rsqrt_approx_f32(narrow_seed(x));
+    double g = x * widen_normal(y);
+    double h = widen_normal(0.5f * y);
+    const double r = fma(-g, h, 0.5);
+    g = fma(g, r, g);
+    h = fma(h, r, h);
+    return fma(fma(-g, g, x), h, g);
 }
 
 }  // namespace pch

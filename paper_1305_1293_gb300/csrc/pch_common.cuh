@@ -36,7 +36,8 @@ constexpr int kHidden = 64;
 struct __align__(16) HERec {
     double L, xc, yc;      // edge length and apex position
     double L1, L2;         // |v1 v2|, |v2 v0|
-    double iL1, iL2, iL;   // reciprocals
+    double iL1, iL2;       // reciprocals of L1, L2
+    double iLq;            // 2^kAngleXBits / L: crossing position -> angle_split units
     int tw1;               // twin of next(h) = (v2 -> v1) in the neighbour: right child's edge
     int tw2;               // twin of prev(h) = (v0 -> v2) in the neighbour: left child's edge
     unsigned v0, v1, v2;   // vertex ids | kPseudoBit
@@ -164,5 +165,15 @@ __device__ __forceinline__ double bitsd(unsigned long long b) { return __longlon
 // 1e-12 and 2e-12 relative, so the test never removes a window the relative margin keeps.
 constexpr unsigned long long kDomUlps = 9008;
 __device__ __forceinline__ bool dominated(double lhs, double rhs) { return dbits(lhs) > dbits(rhs) + kDomUlps; }
+
+// Order tests on the signed 64-bit images of doubles.  For non-NaN x, y of which at least
+// one is >= +0 the images order exactly as the values (a negative operand has a negative
+// image), except that -0 counts below +0.  They run on the integer pipe, which keeps the
+// FP64 unit for arithmetic.
+__device__ __forceinline__ long long sbits(double x) { return __double_as_longlong(x); }
+__device__ __forceinline__ bool lt_s(double x, double y) { return sbits(x) < sbits(y); }
+__device__ __forceinline__ bool le_s(double x, double y) { return sbits(x) <= sbits(y); }
+__device__ __forceinline__ bool gt0_s(double x) { return sbits(x) > 0; }    // x > 0 (NaN: by sign)
+__device__ __forceinline__ bool ge0_s(double x) { return sbits(x) >= 0; }   // x >= +0
 
 }  // namespace pch

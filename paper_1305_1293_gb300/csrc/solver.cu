@@ -38,14 +38,17 @@ __device__ __forceinline__ double ldg_dist(const unsigned long long* g, unsigned
 
 // Pack a (distance to v2, crossing position on the edge) pair for angle_split: the
 // distance is rounded UP to 40 significant bits (so a stored value never understates the
-// window's distance) and the crossing position x/L quantised to 24 bits.
-__device__ __forceinline__ unsigned long long pack_angle(double D, double xs, double iL) {
+// window's distance) and the crossing position, given as xq = 2^24 x / L, floored to 24
+// bits.
+__device__ __forceinline__ unsigned long long pack_angle(double D, double xq) {
     unsigned long long b = dbits(D);
     if (b & kAngleXMask) b = (b | kAngleXMask) + 1ull;
-    double q = floor(xs * iL * (double)(1 << kAngleXBits));
-    q = fmin(fmax(q, 0.0), (double)kAngleXMask);
+    long long q = __double2ll_rd(xq);
+    q = q < 0 ? 0 : (q > (long long)kAngleXMask ? (long long)kAngleXMask : q);
     return (b & ~kAngleXMask) | (unsigned long long)q;
 }
+// kEpsSnap in angle_split units (the snap tolerance kEpsSnap * L times 2^24 / L).
+constexpr double kSplitTol = kEpsSnap * (double)(1 << kAngleXBits);
 
 struct WarpScan {
     int excl, total;
@@ -79,7 +82,7 @@ __device__ __forceinline__ void warp_add_ull(unsigned long long* c, int x) {
 // event lowered the distance of a pseudo-source vertex: the caller then files a fan
 // candidate carrying the event's incoming direction.
 __device__ __forceinline__ bool vertex_event(const Inst& I, unsigned vf, double D, double& gcache) {
-    if (!(D < gcache)) return false;
+    if (!lt_s(D, gcache)) return false;
     unsigned v = vf & ~kPseudoBit;
     unsigned long long nb = dbits(D);
     unsigned long long old = atomicMin(I.g + v, nb);
@@ -352,32 +355,37 @@ struct ChildOut {
     double IA, IB;          // |I A|, |I B| (reused when the child is propagated at once)
 };
 
-// Ray from I' through P' (child frame, both below the child's x axis) meets the axis at
-// X; returns x(X) and |I X| = t |I P|.  Clamped to [0, Lc] with |IX| recomputed there.
-__device__ __forceinline__ void ray_hit(double Ipx, double Ipy, double Ppx, double Ppy, double IP, double Lc,
-                                        double& xh, double& IX) {
-    double den = Ppy - Ipy;
-    double t = -Ipy * rcp_nr(den);
-    xh = Ipx + t * (Ppx - Ipx);
-    IX = t * IP;
-    if (!(den > 0.0) || !(xh >= 0.0 && xh <= Lc)) {
-        xh = den > 0.0 ? fmin(fmax(xh, 0.0), Lc) : (Ppx > Ipx ? Lc : 0.0);
+// The ray from I along D = P - I (P a window endpoint on the parent edge, D = (dx, -py)
+// in the parent frame) meets the child's line O + s u where
+//   s = cross(I - O, D) / cross(u, D),   I + t D with t = cross(I - O, u) / cross(u, D),
+// and cross(I - O, u) = -Ipy.  Inputs: upy = ux py, rpy = rx py, (rx, ry) = I - O.
+// Returns s and |I X| = t |D|; a hit outside [0, Lc] (or a ray that does not cross) is
+// clamped to the nearer end with |I X| recomputed there.
+__device__ __forceinline__ void ray_hit(double dx, double ID, double ux, double uy, double ry, double upy, double rpy,
+                                        double py, double Ipx, double Ipy, double Lc, double& xh, double& IX) {
+    const double den = -fma(uy, dx, upy);   // cross(u, D)
+    const double r = rcp_nr(den);
+    xh = -fma(ry, dx, rpy) * r;             // cross(I - O, D) / cross(u, D)
+    IX = (-Ipy * r) * ID;
+    if (!gt0_s(den) || !(ge0_s(xh) && le_s(xh, Lc))) {
+        xh = gt0_s(den) ? (lt_s(xh, 0.0) ? 0.0 : (lt_s(Lc, xh) ? Lc : xh))
+                        : (gt0_s(fma(ux, dx, -uy * py)) ? Lc : 0.0);   // dot(u, D) > 0: towards Lc
         if (!(xh == xh)) xh = 0.0;
-        double dx = xh - Ipx;
-        IX = sqrt(dx * dx + Ipy * Ipy);
+        const double ex = xh - Ipx;
+        IX = sqrt_nr(fma(ex, ex, Ipy * Ipy));
     }
 }
 
 __device__ __forceinline__ double child_key(double d, double a, double b, double Ipx, double Ipy, double IA,
                                             double IB) {
-    return d + (Ipx < a ? IA : (Ipx > b ? IB : -Ipy));
+    return d + (lt_s(Ipx, a) ? IA : (lt_s(b, Ipx) ? IB : -Ipy));
 }
 
 // dominated(lhs, rhs) with rhs = g + sqrt(q): compares squares, no square root.
 constexpr double kInvDom = 1.0 / (1.0 + kDomRel);
 __device__ __forceinline__ bool dominated_sq(double lhs, double g, double q) {
     const double t = lhs * kInvDom - g;
-    return t > 0.0 && t * t > q;
+    return gt0_s(t) && gt0_s(fma(t, t, -q));
 }
 
 // Algorithm 2 for one window: events, one angle one split, children with the Xin-Wang
@@ -400,55 +408,58 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
         const double py2 = py * py;
         const double ax = A - px, bx = B - px;
         // |IA|, |IB|: carried over from the parent when the window was chained
-        const double IA = IA_in >= 0.0 ? IA_in : sqrt_nr(ax * ax + py2);
-        const double IB = IB_in >= 0.0 ? IB_in : sqrt_nr(bx * bx + py2);
+        const double IA = ge0_s(IA_in) ? IA_in : sqrt_nr(ax * ax + py2);
+        const double IB = ge0_s(IB_in) ? IB_in : sqrt_nr(bx * bx + py2);
         // Xin-Wang endpoint tests against the current distances: the window is
         // useless if the path via v0 beats it at B, or the path via v1 at A.
         if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)) || stale_source(I, src, d))) {
             prop = true;
             const double tol = kEpsSnap * L;
+            const double tiny = kEpsTiny == kEpsSnap ? tol : kEpsTiny * L;
             // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
-            if (A <= tol) {
-                double D0 = d + (A == 0.0 ? IA : sqrt(px * px + py2));
+            if (le_s(A, tol)) {
+                double D0 = d + (sbits(A) == 0 ? IA : sqrt(px * px + py2));
                 if (vertex_event(I, R.v0, D0, g0))   // the ray arrives at v0 from I (h's frame)
                     push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v0 & ~kPseudoBit, D0,
                              I.vphi[h], px, py);
             }
-            if (B >= L - tol) {
+            if (le_s(L - tol, B)) {
                 double q = L - px;
-                double D1 = d + (B == L ? IB : sqrt(q * q + py2));
+                double D1 = d + (sbits(B) == sbits(L) ? IB : sqrt(q * q + py2));
                 if (vertex_event(I, R.v1, D1, g1))   // at v1, in the frame of twin(h) = (v1 -> v0)
                     push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v1 & ~kPseudoBit, D1,
                              I.vphi[R.twin], q, -py);
             }
             // occupancy of v2: the ray I -> v2 crosses e at xs = px + num / den;
-            // decided without the division (den > 0)
+            // decided without the division (den > 0), by the signs of fused residuals
             const double xc = R.xc, yc = R.yc;
             const double den = yc - py, num = (xc - px) * (-py);
-            const bool before_A = num < (A - tol - px) * den;
-            const bool occ = !before_A && num <= (B + tol - px) * den;
+            const bool before_A = gt0_s(fma(ax - tol, den, -num));
+            const bool occ = !before_A && ge0_s(fma(bx + tol, den, -num));
             occ_out = occ;
             bool left, right;
             double Iv2 = 0.0, xcl = 0.0;
             if (occ) {
                 const double xs = px + num * rcp_nr(den);
-                xcl = fmin(fmax(xs, A), B);
+                xcl = lt_s(xs, A) ? A : (lt_s(B, xs) ? B : xs);
+                const double xq = xs * R.iLq;
                 const double dx = xc - px, dy = yc - py;
                 Iv2 = sqrt_nr(dx * dx + dy * dy);
                 const double D2 = d + Iv2;
                 // one angle one split (Fig. `fig:filter`(a)) against angle_split[h]
                 unsigned long long* ap = I.ang + h;
                 const unsigned long long aw = __ldcg(ap);
-                bool win = aw == kEmptyAngle || D2 < bitsd(aw & ~kAngleXMask);
+                bool win = aw == kEmptyAngle || dbits(D2) < (aw & ~kAngleXMask);
                 if (win) {
                     left = right = true;
-                    atomicMin(ap, pack_angle(D2, xs, R.iL));
+                    atomicMin(ap, pack_angle(D2, xq));
                 } else {
-                    // loser: keep the child on its own side of the winner's ray
-                    const double q = (double)(aw & kAngleXMask);
-                    const double sc = L * (1.0 / (double)(1 << kAngleXBits));
-                    left = xs < q * sc - tol;
-                    right = xs > (q + 1.0) * sc + tol;
+                    // loser: keep the child on its own side of the winner's ray, which
+                    // crosses e in [q, q + 1] (angle_split units), widened by the snap
+                    // tolerance
+                    const long long q = (long long)(aw & kAngleXMask);
+                    left = __double2ll_rd(xq + kSplitTol) < q;
+                    right = __double2ll_rd(xq - kSplitTol) > q;
                     if (!left && !right) left = right = true;
                 }
                 if (vertex_event(I, R.v2, D2, g2)) {
@@ -459,8 +470,8 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
                     push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v2 & ~kPseudoBit, D2,
                              I.vphi[hp], ex * ux + ey * uy, ux * ey - uy * ex);
                 }
-                if (B - xcl <= kEpsTiny * L) right = false;
-                if (xcl - A <= kEpsTiny * L) left = false;
+                if (le_s(B - xcl, tiny)) right = false;
+                if (le_s(xcl - A, tiny)) left = false;
             } else {
                 right = before_A;
                 left = !right;
@@ -475,12 +486,15 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
                 if (!(j == 0 ? (right || left) : (right && left))) break;
                 const bool rt = j == 0 && right;
                 ++ncomp;
+                // both sides as one select-driven path (a warp holds left and right children)
                 const double Lc = rt ? R.L1 : R.L2;
+                const double sc = rt ? R.iL1 : R.iL2;
                 const double ox = rt ? xc : 0.0, oy = rt ? yc : 0.0;
-                const double ux = rt ? (L - xc) * R.iL1 : xc * R.iL2;
-                const double uy = rt ? -yc * R.iL1 : yc * R.iL2;
+                const double ux = (rt ? L - xc : xc) * sc;
+                const double uy = (rt ? -yc : yc) * sc;
                 const double rx = px - ox, ry = py - oy;
-                const double Ipx = rx * ux + ry * uy, Ipy = ux * ry - uy * rx;
+                const double Ipx = fma(rx, ux, ry * uy), Ipy = fma(ux, ry, -(uy * rx));
+                const double upy = ux * py, rpy = rx * py;
                 // rays through A and B; at v2 (occupied) the right child starts at 0,
                 // the left child ends at Lc
                 double a, IAc, b, IBc;
@@ -488,30 +502,25 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
                     a = 0.0;
                     IAc = Iv2;
                 } else {
-                    const double qx = A - ox;
-                    ray_hit(Ipx, Ipy, qx * ux - oy * uy, -ux * oy - uy * qx, IA, Lc, a, IAc);
+                    ray_hit(ax, IA, ux, uy, ry, upy, rpy, py, Ipx, Ipy, Lc, a, IAc);
                 }
                 if (occ && !rt) {
                     b = Lc;
                     IBc = Iv2;
                 } else {
-                    const double qx = B - ox;
-                    ray_hit(Ipx, Ipy, qx * ux - oy * uy, -ux * oy - uy * qx, IB, Lc, b, IBc);
+                    ray_hit(bx, IB, ux, uy, ry, upy, rpy, py, Ipx, Ipy, Lc, b, IBc);
                 }
-                if (!(b - a > kEpsTiny * Lc)) continue;
+                if (!lt_s(kEpsTiny * Lc, b - a)) continue;
                 // Xin-Wang filter (Fig. `fig:filter`(b)) on the new window: against its
-                // start and end vertices, and against the vertex of the parent edge that
-                // is not on the child's edge (tested at the endpoint nearer the shared one).
-                bool useless;
-                if (rt) {   // start v2, end v1, third vertex v0 tested at b
-                    const double Xx = xc + b * ux, Xy = yc + b * uy;
-                    useless = dominated(d + IBc, g2 + b) || dominated(d + IAc, g1 + (Lc - a)) ||
-                              dominated_sq(d + IBc, g0, Xx * Xx + Xy * Xy);
-                } else {    // start v0, end v2, third vertex v1 tested at a
-                    const double Xx = a * ux - L, Xy = a * uy;
-                    useless = dominated(d + IBc, g0 + b) || dominated(d + IAc, g2 + (Lc - a)) ||
-                              dominated_sq(d + IAc, g1, Xx * Xx + Xy * Xy);
-                }
+                // start and end vertices (right child: v2, v1; left child: v0, v2), and
+                // against the vertex of the parent edge off the child's edge, tested at the
+                // child's endpoint nearer the shared vertex (right: v0 at b; left: v1 at a).
+                const double gS = rt ? g2 : g0, gE = rt ? g1 : g2, gT = rt ? g0 : g1;
+                const double dA = d + IAc, dB = d + IBc;
+                const double tT = rt ? b : a;
+                const double Xx = fma(tT, ux, rt ? xc : -L), Xy = fma(tT, uy, oy);
+                const bool useless = dominated(dB, gS + b) || dominated(dA, gE + (Lc - a)) ||
+                                     dominated_sq(rt ? dB : dA, gT, fma(Xx, Xx, Xy * Xy));
                 if (useless) continue;
                 const ChildOut co{rt ? R.tw1 : R.tw2, a, b, Ipx, Ipy, child_key(d, a, b, Ipx, Ipy, IAc, IBc), IAc, IBc};
                 if (nch == 0) c0 = co;
@@ -563,9 +572,10 @@ __global__ void __launch_bounds__(256) k_propagate(Work w, int hops) {
         ChildOut c0, c1;
         int nch = 0, occ = 0, ncomp = 0;
         bool prop = false;
+        const bool had = have;
         if (have)
             prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, c0, c1, nch, occ, ncomp, cIA, cIB);
-        bool cont = have && nch > 0 && hop + 1 < hops && c0.key <= w.ctl[inst].tau &&
+        bool cont = have && nch > 0 && hop + 1 < hops && le_s(c0.key, w.ctl[inst].tau) &&
                     *(volatile int*)&cnt->n_child < room;
         const int nwrite = have ? (cont ? nch - 1 : nch) : 0;
         const int slot = warp_reserve(&cnt->n_child, nwrite);
@@ -591,7 +601,7 @@ __global__ void __launch_bounds__(256) k_propagate(Work w, int hops) {
         }
         warp_add_ull(&cnt->propagated, prop ? 1 : 0);
         warp_add_ull(&cnt->chained, cont ? 1 : 0);
-        warp_add_ull(&cnt->examined, have ? 1 : 0);
+        warp_add_ull(&cnt->examined, had ? 1 : 0);
         warp_add_ull(&cnt->occupied, occ);
         warp_add_ull(&cnt->children, ncomp);
     }
@@ -1215,6 +1225,9 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         stats->windows_scanned = (int64_t)c.scanned;
         stats->windows_sorted = (int64_t)c.sorted;
         stats->sort_passes = (cfg.key_bits + kRsDigitBits - 1) / kRsDigitBits;
+        stats->windows_examined = (int64_t)c.examined;
+        stats->windows_occupied = (int64_t)c.occupied;
+        stats->children_computed = (int64_t)c.children;
         // algorithmic FP64 operations of k_propagate (add, sub, mul, div, sqrt = 1; fma = 2),
         // counted per code path of propagate_window: filter 17 (11 for a chained window,
         // whose |IA|, |IB| come from its parent), passed window +11, occupied v2 +20,
@@ -1233,7 +1246,7 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     cfg.k = (opt && opt->k > 0) ? opt->k : default_k();
     cfg.max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : (1LL << 31) - 1;
     cfg.prop_threads = (opt && opt->block > 0) ? opt->block : 256;
-    cfg.prop_blocks_per_sm = 4;
+    cfg.prop_blocks_per_sm = default_prop_blocks_per_sm();
     cfg.trim = !(opt && (opt->flags & PCH_FLAG_NO_TRIM));
     cfg.full_fan = (opt && (opt->flags & PCH_FLAG_FULL_FAN)) ? 1 : 0;
     cfg.profile = (opt && (opt->flags & PCH_FLAG_PROFILE)) ? 1 : 0;
@@ -1474,7 +1487,7 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
     std::vector<long long> ks;
     for (long long k = 24576; k <= std::max<long long>(24576, 8LL * m->dm.nf); k *= 4) ks.push_back(k);
     const int blocks[2] = {128, 256};
-    const int hopss[4] = {1, 2, 4, 8};
+    const int hopss[5] = {2, 4, 8, 16, 32};
     for (long long k : ks) {
         for (int b : blocks) {
             for (int hp : hopss) {
