@@ -194,11 +194,12 @@ pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float
                            int32_t* n_rows);
 
 /* ---- autotuner (build-only) ------------------------------------------------------------
- * Times full solves of `src` on `m` over a grid of windows-per-iteration k (24576 times
- * powers of 4, up to 8x the face count), propagation block sizes (128, 256) and hops
- * (2, 4, 8, 16, 32), and writes the fastest into opt->k, opt->block and opt->hops (the other
- * fields of *opt are kept and used for every trial).  If cache_path is not NULL the result is looked up first
- * in, and then appended to, that text file, keyed by GPU name and mesh size, so a
+ * Times full solves of `src` on `m` by a coordinate search: windows-per-iteration k
+ * (24576 times powers of 4, up to 8x the face count) at block 128 and 16 hops, then hops
+ * (4, 8, 16, 32, 64), then propagation block sizes (64, 128, 256), and writes the fastest
+ * into opt->k, opt->block and opt->hops (the other fields of *opt are kept and used for
+ * every trial).  If cache_path is not NULL the result is looked up first in, and then
+ * appended to, that text file, keyed by GPU name and mesh size, so a
  * second call does no timing.  Errors: as pch_solve. */
 pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_options* opt, const char* cache_path,
                         double* best_ms);

@@ -388,32 +388,52 @@ __device__ __forceinline__ bool dominated_sq(double lhs, double g, double q) {
     return gt0_s(t) && gt0_s(fma(t, t, -q));
 }
 
+// The round's write side of the propagation kernel's shared-memory queue: the second
+// child of a window whose rays reach v2 is deferred there as a task, so that each lane
+// computes one child per round.
+struct TaskQueue {
+    double *d, *A, *B, *px, *py, *IA, *IB;
+    int *he, *inst, *src, *hop;
+    int* count;   // entries reserved this round
+    int cap;      // entries the next round can take
+};
+constexpr int kHopTask = 1 << 30;   // hop-field flag of a queue entry: a deferred left child
+
 // Algorithm 2 for one window: events, one angle one split, children with the Xin-Wang
-// filter.  Returns whether the window passed the filter; children in c0, c1 (nch).
+// filter.  Returns whether the window passed the filter; children in c0, c1 (nch).  When
+// both children exist the left one is deferred to q as a task (if q has room).  A task
+// (task = true) skips the window's own part, done in an earlier round, and computes the
+// left child only; IB_in then holds |I v2|.
 __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, int2* req, double4* req_d, int inst,
                                                  int src, double d, int h, double A, double B, double px, double py,
-                                                 ChildOut& c0, ChildOut& c1, int& nch, int& occ_out, int& ncomp,
-                                                 double IA_in, double IB_in) {
+                                                 bool task, int hop, const TaskQueue& q, ChildOut& c0, ChildOut& c1,
+                                                 int& nch, int& occ_out, int& ncomp, double IA_in, double IB_in) {
     bool prop = false;
     nch = 0;
     occ_out = 0;
     ncomp = 0;
-        {
+    {
         const Inst& I = w.inst[inst];
         const HERec R = I.rec[h];
         const double L = R.L;
         double g0 = ldg_dist(I.g, R.v0 & ~kPseudoBit);
         double g1 = ldg_dist(I.g, R.v1 & ~kPseudoBit);
         double g2 = ldg_dist(I.g, R.v2 & ~kPseudoBit);
-        const double py2 = py * py;
         const double ax = A - px, bx = B - px;
         // |IA|, |IB|: carried over from the parent when the window was chained
-        const double IA = ge0_s(IA_in) ? IA_in : sqrt_nr(ax * ax + py2);
-        const double IB = ge0_s(IB_in) ? IB_in : sqrt_nr(bx * bx + py2);
-        // Xin-Wang endpoint tests against the current distances: the window is
-        // useless if the path via v0 beats it at B, or the path via v1 at A.
-        if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)) || stale_source(I, src, d))) {
+        const double IA = ge0_s(IA_in) ? IA_in : sqrt_nr(fma(ax, ax, py * py));
+        const double IB = ge0_s(IB_in) ? IB_in : sqrt_nr(fma(bx, bx, py * py));
+        const double xc = R.xc, yc = R.yc;
+        bool left = false, right = false, occ = false;
+        double Iv2 = IB;
+        if (task) {
+            occ = true;
+            left = R.tw2 >= 0;
+        } else if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)) || stale_source(I, src, d))) {
+            // Xin-Wang endpoint tests against the current distances passed: the window is
+            // useless if the path via v0 beats it at B, or the path via v1 at A
             prop = true;
+            const double py2 = py * py;
             const double tol = kEpsSnap * L;
             const double tiny = kEpsTiny == kEpsSnap ? tol : kEpsTiny * L;
             // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
@@ -432,16 +452,13 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
             }
             // occupancy of v2: the ray I -> v2 crosses e at xs = px + num / den;
             // decided without the division (den > 0), by the signs of fused residuals
-            const double xc = R.xc, yc = R.yc;
             const double den = yc - py, num = (xc - px) * (-py);
             const bool before_A = gt0_s(fma(ax - tol, den, -num));
-            const bool occ = !before_A && ge0_s(fma(bx + tol, den, -num));
+            occ = !before_A && ge0_s(fma(bx + tol, den, -num));
             occ_out = occ;
-            bool left, right;
-            double Iv2 = 0.0, xcl = 0.0;
             if (occ) {
                 const double xs = px + num * rcp_nr(den);
-                xcl = lt_s(xs, A) ? A : (lt_s(B, xs) ? B : xs);
+                const double xcl = lt_s(xs, A) ? A : (lt_s(B, xs) ? B : xs);
                 const double xq = xs * R.iLq;
                 const double dx = xc - px, dy = yc - py;
                 Iv2 = sqrt_nr(dx * dx + dy * dy);
@@ -478,12 +495,23 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
             }
             right = right && R.tw1 >= 0;
             left = left && R.tw2 >= 0;
+        }
+        {
             // Children, one code path in child order (right first): the right child
             // lies on edge v2 -> v1 (frame origin v2), the left on v0 -> v2 (origin v0).
             // When v2 is occupied the child's endpoint at v2 is exact.
 #pragma unroll 1
             for (int j = 0; j < 2; ++j) {
                 if (!(j == 0 ? (right || left) : (right && left))) break;
+                if (j == 1) {   // defer the left child: one child per lane and round
+                    const int ts = atomicAdd(q.count, 1);
+                    if (ts < q.cap) {
+                        q.he[ts] = h; q.inst[ts] = inst; q.src[ts] = src; q.hop[ts] = hop | kHopTask;
+                        q.d[ts] = d; q.A[ts] = A; q.B[ts] = B; q.px[ts] = px; q.py[ts] = py;
+                        q.IA[ts] = IA; q.IB[ts] = Iv2;
+                        break;
+                    }
+                }
                 const bool rt = j == 0 && right;
                 ++ncomp;
                 // both sides as one select-driven path (a warp holds left and right children)
@@ -532,76 +560,123 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
     return prop;
 }
 
-// Persistent propagation over the work list.  Lanes without a window take the next one
-// from a warp-aggregated counter; a lane whose window produced a child with key inside
-// this iteration's band (key <= tau) propagates that child at once, up to `hops`
-// windows per chain, while the child arena stays below half full.
-__global__ void __launch_bounds__(256) k_propagate(Work w, int hops) {
+// Windows in flight per block: the shared-memory queue of chained children holds at most
+// one window per thread, in two buffers (read / written by alternate rounds) of 7 doubles
+// and 4 ints per entry.
+constexpr int kPropMaxBlock = 256;
+constexpr int kPropQueueBytesPerThread = 2 * (7 * 8 + 4 * 4);
+
+// Step 3 of the iteration (Algorithm 2 over the selected windows), persistent.  The block
+// advances in lock-step rounds: in each round lane t takes queue entry t (a child chained
+// from the previous round, key <= tau, at most `hops` hops from its selected ancestor) or
+// else a fresh selected window; children that continue are pushed back into the queue
+// (chaining stops while the child arena is half full).
+// Repacking the chains onto the lowest lanes every round keeps the warps that do issue
+// FP64 work full once the selected list runs dry, and leaves the other warps idle.
+__global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops) {
+    extern __shared__ double q_mem[];   // blockDim.x * kPropQueueBytesPerThread bytes
+    const int QB = 2 * blockDim.x;
+    double* q_d = q_mem;
+    double* q_A = q_d + QB;
+    double* q_B = q_A + QB;
+    double* q_px = q_B + QB;
+    double* q_py = q_px + QB;
+    double* q_IA = q_py + QB;
+    double* q_IB = q_IA + QB;
+    int* q_he = reinterpret_cast<int*>(q_IB + QB);
+    int* q_inst = q_he + QB;
+    int* q_src = q_inst + QB;
+    int* q_hop = q_src + QB;
+    // Round r reads s_nq[r % 3] / s_dry[r % 3], writes slot (r + 1) % 3 and clears slot
+    // (r + 2) % 3 (read in round r - 1, written in round r + 1), so no slot is written in
+    // the round that reads it and every decision taken from them is uniform over the block.
+    __shared__ int s_nq[3];      // queue sizes
+    __shared__ int s_dry[3];     // the selected list is exhausted
     Counters* cnt = w.cnt;
     if (cnt->halt) return;
     const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31;
+    const int t = threadIdx.x;
+    const int lane = t & 31;
     const unsigned lt = (1u << lane) - 1u;
     const int it = cnt->iter;
     const int n = min(cnt->n_sel, w.sel_cap);
     int2* req = w.req[it & 1];
     double4* req_d = w.req_d[it & 1];
     const int room = w.arena_cap / 2 - 2 * (int)(gridDim.x * blockDim.x);
-    bool have = false, exhausted = false;
-    int h = 0, inst = 0, src = -1, hop = 0;
-    double d = 0.0, A = 0.0, B = 0.0, px = 0.0, py = 0.0, cIA = -1.0, cIB = -1.0;
-    while (true) {
+    if (t == 0) {
+        for (int i = 0; i < 3; ++i) s_nq[i] = s_dry[i] = 0;
+    }
+    for (int r = 0;; ++r) {
+        const int rb = r & 1, wb = rb ^ 1;
+        __syncthreads();   // last round's pushes and s_dry are visible; its reads are done
+        const int nq = min(s_nq[r % 3], (int)blockDim.x);
+        const bool dry = s_dry[r % 3] != 0;
+        if (nq == 0 && dry) break;                 // uniform over the block
+        if (t == 0) {
+            s_nq[(r + 2) % 3] = 0;
+            s_dry[(r + 2) % 3] = 0;
+            if (dry) s_dry[(r + 1) % 3] = 1;
+        }
+        bool have = t < nq, task = false;
+        int h = 0, inst = 0, src = -1, hop = 0;
+        double d = 0.0, A = 0.0, B = 0.0, px = 0.0, py = 0.0, cIA = -1.0, cIB = -1.0;
+        if (have) {
+            h = q_he[rb * blockDim.x + t]; inst = q_inst[rb * blockDim.x + t]; src = q_src[rb * blockDim.x + t]; hop = q_hop[rb * blockDim.x + t];
+            task = (hop & kHopTask) != 0;
+            hop &= ~kHopTask;
+            d = q_d[rb * blockDim.x + t]; A = q_A[rb * blockDim.x + t]; B = q_B[rb * blockDim.x + t]; px = q_px[rb * blockDim.x + t]; py = q_py[rb * blockDim.x + t];
+            cIA = q_IA[rb * blockDim.x + t]; cIB = q_IB[rb * blockDim.x + t];
+        }
         const unsigned need = __ballot_sync(full, !have);
-        if (need && !exhausted) {
+        if (need && !dry) {
             int base = 0;
             if (lane == 0) base = atomicAdd(&cnt->work_next, __popc(need));
             base = __shfl_sync(full, base, 0);
-            if (base >= n) exhausted = true;
+            if (base + __popc(need) >= n && lane == 0) s_dry[(r + 1) % 3] = 1;
             if (!have) {
                 const int idx = base + __popc(need & lt);
                 if (idx < n) {
                     h = w.sel.he[idx]; inst = w.sel.inst[idx]; d = w.sel.d[idx]; src = w.sel.src[idx];
                     A = w.sel.A[idx]; B = w.sel.B[idx]; px = w.sel.px[idx]; py = w.sel.py[idx];
-                    cIA = cIB = -1.0;
                     have = true;
-                    hop = 0;
                 }
             }
         }
-        if (!__any_sync(full, have)) break;
+        if (!__any_sync(full, have)) continue;     // this warp idles this round
         ChildOut c0, c1;
         int nch = 0, occ = 0, ncomp = 0;
         bool prop = false;
-        const bool had = have;
+        const int wo = wb * blockDim.x;
+        const TaskQueue tq{q_d + wo, q_A + wo, q_B + wo, q_px + wo, q_py + wo, q_IA + wo, q_IB + wo,
+                           q_he + wo, q_inst + wo, q_src + wo, q_hop + wo, &s_nq[(r + 1) % 3], (int)blockDim.x};
         if (have)
-            prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, c0, c1, nch, occ, ncomp, cIA, cIB);
+            prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, task, hop, tq, c0, c1, nch, occ,
+                                    ncomp, cIA, cIB);
         bool cont = have && nch > 0 && hop + 1 < hops && le_s(c0.key, w.ctl[inst].tau) &&
                     *(volatile int*)&cnt->n_child < room;
+        // the continuing child goes to the queue while it has room, every other child to
+        // the arena
+        const int qs = warp_reserve(&s_nq[(r + 1) % 3], cont ? 1 : 0);
+        if (cont && qs >= (int)blockDim.x) cont = false;
+        if (cont) {
+            q_he[wb * blockDim.x + qs] = c0.he; q_inst[wb * blockDim.x + qs] = inst; q_src[wb * blockDim.x + qs] = src; q_hop[wb * blockDim.x + qs] = hop + 1;
+            q_d[wb * blockDim.x + qs] = d; q_A[wb * blockDim.x + qs] = c0.A; q_B[wb * blockDim.x + qs] = c0.B; q_px[wb * blockDim.x + qs] = c0.px; q_py[wb * blockDim.x + qs] = c0.py;
+            q_IA[wb * blockDim.x + qs] = c0.IA; q_IB[wb * blockDim.x + qs] = c0.IB;
+        }
         const int nwrite = have ? (cont ? nch - 1 : nch) : 0;
         const int slot = warp_reserve(&cnt->n_child, nwrite);
-        if (cont) {
-            if (nch > 1) {
-                if (slot < w.arena_cap) store_win(w.arena, slot, c1.he, inst, d, c1.A, c1.B, c1.px, c1.py, c1.key, src);
-                else atomicOr(&cnt->error, kErrPoolFull);
-            }
-            h = c0.he; A = c0.A; B = c0.B; px = c0.px; py = c0.py;
-            cIA = c0.IA; cIB = c0.IB;
-            ++hop;
-        } else if (have) {
-            if (nch > 0) {
-                if (slot < w.arena_cap) store_win(w.arena, slot, c0.he, inst, d, c0.A, c0.B, c0.px, c0.py, c0.key, src);
-                else atomicOr(&cnt->error, kErrPoolFull);
-            }
-            if (nch > 1) {
-                if (slot + 1 < w.arena_cap)
-                    store_win(w.arena, slot + 1, c1.he, inst, d, c1.A, c1.B, c1.px, c1.py, c1.key, src);
-                else atomicOr(&cnt->error, kErrPoolFull);
-            }
-            have = false;
+        if (nwrite > 0) {
+            const ChildOut& cf = cont ? c1 : c0;
+            if (slot < w.arena_cap) store_win(w.arena, slot, cf.he, inst, d, cf.A, cf.B, cf.px, cf.py, cf.key, src);
+            else atomicOr(&cnt->error, kErrPoolFull);
+        }
+        if (nwrite > 1) {
+            if (slot + 1 < w.arena_cap) store_win(w.arena, slot + 1, c1.he, inst, d, c1.A, c1.B, c1.px, c1.py, c1.key, src);
+            else atomicOr(&cnt->error, kErrPoolFull);
         }
         warp_add_ull(&cnt->propagated, prop ? 1 : 0);
         warp_add_ull(&cnt->chained, cont ? 1 : 0);
-        warp_add_ull(&cnt->examined, had ? 1 : 0);
+        warp_add_ull(&cnt->examined, have && !task ? 1 : 0);
         warp_add_ull(&cnt->occupied, occ);
         warp_add_ull(&cnt->children, ncomp);
     }
@@ -1084,7 +1159,8 @@ static cudaError_t launch_iteration(Workspace* ws, cudaStream_t s, const SolveCf
     k_tau<<<std::min(w.n_inst, 1024), 256, 0, s>>>(w, cfg.control, cfg.mlp);
     k_compact<<<grid_for(4), tpb, 0, s>>>(w);
     if (ev) cudaEventRecord(ev[1], s);
-    k_propagate<<<grid_for(cfg.prop_blocks_per_sm), cfg.prop_threads, 0, s>>>(w, cfg.hops);
+    k_propagate<<<grid_for(cfg.prop_blocks_per_sm), cfg.prop_threads, cfg.prop_threads * kPropQueueBytesPerThread, s>>>(
+        w, cfg.hops);
     if (ev) cudaEventRecord(ev[2], s);
     k_fan<<<grid_for(2), 256, 0, s>>>(w, cfg.full_fan);
     if (ev) cudaEventRecord(ev[3], s);
@@ -1246,7 +1322,7 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     cfg.k = (opt && opt->k > 0) ? opt->k : default_k();
     cfg.max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : (1LL << 31) - 1;
     cfg.prop_threads = (opt && opt->block > 0) ? opt->block : 256;
-    cfg.prop_blocks_per_sm = default_prop_blocks_per_sm();
+    cfg.prop_blocks_per_sm = default_prop_blocks_per_sm(cfg.prop_threads);
     cfg.trim = !(opt && (opt->flags & PCH_FLAG_NO_TRIM));
     cfg.full_fan = (opt && (opt->flags & PCH_FLAG_FULL_FAN)) ? 1 : 0;
     cfg.profile = (opt && (opt->flags & PCH_FLAG_PROFILE)) ? 1 : 0;
@@ -1486,25 +1562,36 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
     int best_b = 0, best_h = 0;
     std::vector<long long> ks;
     for (long long k = 24576; k <= std::max<long long>(24576, 8LL * m->dm.nf); k *= 4) ks.push_back(k);
-    const int blocks[2] = {128, 256};
-    const int hopss[5] = {2, 4, 8, 16, 32};
-    for (long long k : ks) {
-        for (int b : blocks) {
-            for (int hp : hopss) {
-                trial.k = k;
-                trial.block = b;
-                trial.hops = hp;
-                double ms_sum = 0.0;
-                for (int rep = 0; rep < 2; ++rep) {   // first run warms the graph cache
-                    pch_stats st{};
-                    pch_status rc = solve_instances(&m, 1, &sd, 1, &trial, nullptr, kOutNone, &st);
-                    if (rc != PCH_OK) return rc;
-                    if (rep == 1) ms_sum = st.ms_total;
-                }
-                if (ms_sum < best) { best = ms_sum; best_k = k; best_b = b; best_h = hp; }
-            }
+    const int blocks[3] = {64, 128, 256};
+    const int hopss[5] = {4, 8, 16, 32, 64};
+    auto time_cfg = [&](long long k, int b, int hp, double& ms) -> pch_status {
+        trial.k = k;
+        trial.block = b;
+        trial.hops = hp;
+        for (int rep = 0; rep < 2; ++rep) {   // the first run warms the graph cache
+            pch_stats st{};
+            pch_status rc = solve_instances(&m, 1, &sd, 1, &trial, nullptr, kOutNone, &st);
+            if (rc != PCH_OK) return rc;
+            ms = st.ms_total;
         }
-    }
+        return PCH_OK;
+    };
+    auto consider = [&](long long k, int b, int hp) -> pch_status {
+        double ms = 0.0;
+        pch_status rc = time_cfg(k, b, hp, ms);
+        if (rc == PCH_OK && ms < best) { best = ms; best_k = k; best_b = b; best_h = hp; }
+        return rc;
+    };
+    // coordinate search: k at (128, 16), then hops, then the block size
+    pch_status rc = PCH_OK;
+    for (long long k : ks)
+        if ((rc = consider(k, 128, 16)) != PCH_OK) return rc;
+    const long long k_sel = best_k;
+    for (int hp : hopss)
+        if (hp != 16 && (rc = consider(k_sel, 128, hp)) != PCH_OK) return rc;
+    const int h_sel = best_h;
+    for (int b : blocks)
+        if (b != 128 && (rc = consider(k_sel, b, h_sel)) != PCH_OK) return rc;
     opt->k = best_k;
     opt->block = best_b;
     opt->hops = best_h;

@@ -29,7 +29,7 @@ enum { kOutHost = 0, kOutDevice = 1, kOutNone = 2 };
 
 long long default_k();
 int default_hops();
-int default_prop_blocks_per_sm();
+int default_prop_blocks_per_sm(int block);
 const float* mlp_device_params();
 
 pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* srcs, int n_src,
