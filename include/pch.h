@@ -79,10 +79,11 @@ typedef struct {
     int64_t max_iters;        /* iteration cap; exceeded -> PCH_ERR_TIMEOUT (default 2^31) */
     void* stream;             /* cudaStream_t to run on (NULL = legacy default stream) */
     int32_t out_on_device;    /* nonzero: output pointers are device pointers */
-    int32_t block;            /* threads per block of the propagation kernel (0 = tuned) */
+    int32_t block;            /* threads per block of the propagation kernel, a multiple of 32
+                                 in [32, 256] (0 = default 64) */
     int32_t flags;            /* PCH_FLAG_* */
     int32_t hops;             /* windows one propagation lane may chain within an iteration's
-                                 band (1 = the paper's one hop per iteration; 0 = default) */
+                                 band (1 = the paper's one hop per iteration; 0 = default 32) */
 } pch_options;
 
 enum {
@@ -195,7 +196,8 @@ pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float
 
 /* ---- autotuner (build-only) ------------------------------------------------------------
  * Times full solves of `src` on `m` by a coordinate search: windows-per-iteration k
- * (24576 times powers of 4, up to 8x the face count) at block 128 and 16 hops, then hops
+ * (24576 times powers of 4, up to 8x the face count, from the largest down until one is twice
+ * as slow as the best) at block 128 and 16 hops, then hops
  * (4, 8, 16, 32, 64), then propagation block sizes (64, 128, 256), and writes the fastest
  * into opt->k, opt->block and opt->hops (the other fields of *opt are kept and used for
  * every trial).  If cache_path is not NULL the result is looked up first in, and then

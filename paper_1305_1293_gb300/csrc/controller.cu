@@ -32,7 +32,7 @@ int default_hops() {
         int v = std::atoi(e);
         if (v > 0) return v;
     }
-    return 4;
+    return 32;
 }
 
 // Resident propagation blocks per SM: 512 threads per SM (16 warps of 128 registers a

@@ -1321,7 +1321,7 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     cfg.loop = opt ? opt->loop : PCH_LOOP_GRAPH;
     cfg.k = (opt && opt->k > 0) ? opt->k : default_k();
     cfg.max_iters = (opt && opt->max_iters > 0) ? opt->max_iters : (1LL << 31) - 1;
-    cfg.prop_threads = (opt && opt->block > 0) ? opt->block : 256;
+    cfg.prop_threads = (opt && opt->block > 0) ? opt->block : 64;
     cfg.prop_blocks_per_sm = default_prop_blocks_per_sm(cfg.prop_threads);
     cfg.trim = !(opt && (opt->flags & PCH_FLAG_NO_TRIM));
     cfg.full_fan = (opt && (opt->flags & PCH_FLAG_FULL_FAN)) ? 1 : 0;
@@ -1582,10 +1582,15 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
         if (rc == PCH_OK && ms < best) { best = ms; best_k = k; best_b = b; best_h = hp; }
         return rc;
     };
-    // coordinate search: k at (128, 16), then hops, then the block size
+    // coordinate search: k at (128, 16) from the largest down (stopping once a k is twice as
+    // slow as the best: smaller ones only add iterations), then hops, then the block size
     pch_status rc = PCH_OK;
-    for (long long k : ks)
-        if ((rc = consider(k, 128, 16)) != PCH_OK) return rc;
+    for (auto it = ks.rbegin(); it != ks.rend(); ++it) {
+        double ms = 0.0;
+        if ((rc = time_cfg(*it, 128, 16, ms)) != PCH_OK) return rc;
+        if (ms < best) { best = ms; best_k = *it; best_b = 128; best_h = 16; }
+        if (ms > 2.0 * best) break;
+    }
     const long long k_sel = best_k;
     for (int hp : hopss)
         if (hp != 16 && (rc = consider(k_sel, 128, hp)) != PCH_OK) return rc;
