@@ -35,6 +35,15 @@ int default_hops() {
     return 32;
 }
 
+int default_tail_cut() {
+    const char* e = std::getenv("PCH_TAIL_CUT");
+    if (e) {
+        int v = std::atoi(e);
+        if (v >= 0) return v;
+    }
+    return 0;
+}
+
 // Resident propagation blocks per SM: 512 threads per SM (16 warps of 128 registers a
 // thread fill the register file), unless PCH_PROP_BLOCKS_PER_SM says otherwise.
 int default_prop_blocks_per_sm(int block) {

@@ -69,6 +69,8 @@ struct WinSoA {
     double* py;
     double* key;    // d + dist(I, [A, B]): the window's distance back to the source
     int* src;       // mesh vertex at the pseudo-source (-1 for a point inside a face)
+    double* IA;     // |I A|, |I B| (kept so that propagation never recomputes them)
+    double* IB;
 };
 
 // ---- instances -------------------------------------------------------------------

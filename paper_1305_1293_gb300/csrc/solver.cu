@@ -169,14 +169,14 @@ __device__ __forceinline__ void pool_stat(const Work& w, const PoolStats& ps, in
 }
 
 __device__ __forceinline__ void load_win(const WinSoA& s, int i, int& he, int& inst, double& d, double& A, double& B,
-                                         double& px, double& py, double& key, int& src) {
+                                         double& px, double& py, double& key, int& src, double& IA, double& IB) {
     he = s.he[i]; inst = s.inst[i]; d = s.d[i]; A = s.A[i]; B = s.B[i]; px = s.px[i]; py = s.py[i]; key = s.key[i];
-    src = s.src[i];
+    src = s.src[i]; IA = s.IA[i]; IB = s.IB[i];
 }
 __device__ __forceinline__ void store_win(const WinSoA& s, int i, int he, int inst, double d, double A, double B,
-                                          double px, double py, double key, int src) {
+                                          double px, double py, double key, int src, double IA, double IB) {
     s.he[i] = he; s.inst[i] = inst; s.d[i] = d; s.A[i] = A; s.B[i] = B; s.px[i] = px; s.py[i] = py; s.key[i] = key;
-    s.src[i] = src;
+    s.src[i] = src; s.IA[i] = IA; s.IB[i] = IB;
 }
 
 // A window whose pseudo-source vertex has since been reached by a shorter path is
@@ -235,10 +235,10 @@ __global__ void k_init_face_sources(Work w, const SrcDev* __restrict__ srcs, int
             if (R.twin < 0) continue;
             // window on twin(h) = (v1 -> v0): point at (L - x, -y), interval [0, L]
             double px = R.L - x, py = -y;
-            double key = px < 0 ? sqrt(px * px + py * py)
-                                : (px > R.L ? sqrt((px - R.L) * (px - R.L) + py * py) : -py);
+            const double IA = sqrt(px * px + py * py), IB = sqrt((px - R.L) * (px - R.L) + py * py);
+            double key = px < 0 ? IA : (px > R.L ? IB : -py);
             int slot = atomicAdd(&cnt->n_child, 1);
-            if (slot < w.arena_cap) store_win(w.arena, slot, R.twin, s.inst, 0.0, 0.0, R.L, px, py, key, -1);
+            if (slot < w.arena_cap) store_win(w.arena, slot, R.twin, s.inst, 0.0, 0.0, R.L, px, py, key, -1, IA, IB);
         }
     }
 }
@@ -327,18 +327,18 @@ __global__ void __launch_bounds__(256) k_compact(Work w) {
         int i = base + threadIdx.x;
         bool valid = i < n;
         int he = 0, inst = 0, src = -1;
-        double d = 0, A = 0, B = 0, px = 0, py = 0, key = 0;
+        double d = 0, A = 0, B = 0, px = 0, py = 0, key = 0, IA = 0, IB = 0;
         if (valid) {
-            load_win(cur, i, he, inst, d, A, B, px, py, key, src);
+            load_win(cur, i, he, inst, d, A, B, px, py, key, src, IA, IB);
             if (stale_source(w.inst[inst], src, d)) valid = false;   // dropped from the pool
         }
         bool sel = valid && key <= w.ctl[inst].tau;
         int slot = warp_reserve(&cnt->n_sel, sel ? 1 : 0);
         if (sel && slot >= w.sel_cap) sel = false;   // work list full: stays pending
-        if (sel) store_win(w.sel, slot, he, inst, d, A, B, px, py, key, src);
+        if (sel) store_win(w.sel, slot, he, inst, d, A, B, px, py, key, src, IA, IB);
         bool rest = valid && !sel;
         int rslot = warp_reserve(&cnt->n_rest, rest ? 1 : 0);
-        if (rest) store_win(nxt, rslot, he, inst, d, A, B, px, py, key, src);
+        if (rest) store_win(nxt, rslot, he, inst, d, A, B, px, py, key, src, IA, IB);
         pool_stat(w, ps, inst, key, rest);
     }
     if (ps.sh_hist) {
@@ -573,7 +573,7 @@ constexpr int kPropQueueBytesPerThread = 2 * (7 * 8 + 4 * 4);
 // (chaining stops while the child arena is half full).
 // Repacking the chains onto the lowest lanes every round keeps the warps that do issue
 // FP64 work full once the selected list runs dry, and leaves the other warps idle.
-__global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops) {
+__global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops, int tail_cut) {
     extern __shared__ double q_mem[];   // blockDim.x * kPropQueueBytesPerThread bytes
     const int QB = 2 * blockDim.x;
     double* q_d = q_mem;
@@ -638,6 +638,7 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
                 if (idx < n) {
                     h = w.sel.he[idx]; inst = w.sel.inst[idx]; d = w.sel.d[idx]; src = w.sel.src[idx];
                     A = w.sel.A[idx]; B = w.sel.B[idx]; px = w.sel.px[idx]; py = w.sel.py[idx];
+                    cIA = w.sel.IA[idx]; cIB = w.sel.IB[idx];
                     have = true;
                 }
             }
@@ -653,7 +654,7 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
             prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, task, hop, tq, c0, c1, nch, occ,
                                     ncomp, cIA, cIB);
         bool cont = have && nch > 0 && hop + 1 < hops && le_s(c0.key, w.ctl[inst].tau) &&
-                    *(volatile int*)&cnt->n_child < room;
+                    (!dry || nq >= tail_cut) && *(volatile int*)&cnt->n_child < room;
         // the continuing child goes to the queue while it has room, every other child to
         // the arena
         const int qs = warp_reserve(&s_nq[(r + 1) % 3], cont ? 1 : 0);
@@ -667,11 +668,13 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
         const int slot = warp_reserve(&cnt->n_child, nwrite);
         if (nwrite > 0) {
             const ChildOut& cf = cont ? c1 : c0;
-            if (slot < w.arena_cap) store_win(w.arena, slot, cf.he, inst, d, cf.A, cf.B, cf.px, cf.py, cf.key, src);
+            if (slot < w.arena_cap)
+                store_win(w.arena, slot, cf.he, inst, d, cf.A, cf.B, cf.px, cf.py, cf.key, src, cf.IA, cf.IB);
             else atomicOr(&cnt->error, kErrPoolFull);
         }
         if (nwrite > 1) {
-            if (slot + 1 < w.arena_cap) store_win(w.arena, slot + 1, c1.he, inst, d, c1.A, c1.B, c1.px, c1.py, c1.key, src);
+            if (slot + 1 < w.arena_cap)
+                store_win(w.arena, slot + 1, c1.he, inst, d, c1.A, c1.B, c1.px, c1.py, c1.key, src, c1.IA, c1.IB);
             else atomicOr(&cnt->error, kErrPoolFull);
         }
         warp_add_ull(&cnt->propagated, prop ? 1 : 0);
@@ -839,7 +842,7 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                 continue;
             }
             const double key = D + (px < A ? IA : (px > B ? IB : -py));
-            store_win(w.arena, sl, Ro.twin, inst, D, A, B, px, py, key, (int)v);
+            store_win(w.arena, sl, Ro.twin, inst, D, A, B, px, py, key, (int)v, IA, IB);
             atomicAdd(&cnt->fan_windows, 1ull);
         }
     }
@@ -866,10 +869,10 @@ __global__ void __launch_bounds__(256) k_append(Work w, const unsigned* __restri
         unsigned k = i < n ? keys[i] : ~0u;
         bool keep = k != ~0u;
         int he = 0, inst = 0, src = -1;
-        double d = 0, A = 0, B = 0, px = 0, py = 0, key = 0;
+        double d = 0, A = 0, B = 0, px = 0, py = 0, key = 0, IA = 0, IB = 0;
         int trimmed = 0;
         if (keep) {
-            load_win(w.arena, vals[i], he, inst, d, A, B, px, py, key, src);
+            load_win(w.arena, vals[i], he, inst, d, A, B, px, py, key, src, IA, IB);
             const Inst& I = w.inst[inst];
             const HERec R = I.rec[he];
             // re-filter against the distances after this iteration's events (the window
@@ -897,7 +900,7 @@ __global__ void __launch_bounds__(256) k_append(Work w, const unsigned* __restri
         int slot = warp_reserve(&cnt->n_app, keep ? 1 : 0);
         if (keep) {
             int pos = n_rest + slot;
-            if (pos < w.pool_cap) store_win(nxt, pos, he, inst, d, A, B, px, py, key, src);
+            if (pos < w.pool_cap) store_win(nxt, pos, he, inst, d, A, B, px, py, key, src, IA, IB);
             else atomicOr(&cnt->error, kErrPoolFull);
         }
         pool_stat(w, ps, inst, key, keep);
@@ -1023,6 +1026,8 @@ static cudaError_t alloc_soa(Alloc& a, WinSoA& s, int cap) {
     if ((e = a.get(&s.px, cap))) return e;
     if ((e = a.get(&s.py, cap))) return e;
     if ((e = a.get(&s.key, cap))) return e;
+    if ((e = a.get(&s.IA, cap))) return e;
+    if ((e = a.get(&s.IB, cap))) return e;
     return a.get(&s.src, cap);
 }
 
@@ -1071,6 +1076,8 @@ static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap) {
             cudaMemcpy(nw.pool[p].py, w.pool[p].py, n * 8, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.pool[p].key, w.pool[p].key, n * 8, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.pool[p].src, w.pool[p].src, n * 4, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].IA, w.pool[p].IA, n * 8, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.pool[p].IB, w.pool[p].IB, n * 8, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.req[p], w.req[p], sizeof(int2) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.req_d[p], w.req_d[p], sizeof(double4) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
         }
@@ -1160,7 +1167,7 @@ static cudaError_t launch_iteration(Workspace* ws, cudaStream_t s, const SolveCf
     k_compact<<<grid_for(4), tpb, 0, s>>>(w);
     if (ev) cudaEventRecord(ev[1], s);
     k_propagate<<<grid_for(cfg.prop_blocks_per_sm), cfg.prop_threads, cfg.prop_threads * kPropQueueBytesPerThread, s>>>(
-        w, cfg.hops);
+        w, cfg.hops, cfg.tail_cut);
     if (ev) cudaEventRecord(ev[2], s);
     k_fan<<<grid_for(2), 256, 0, s>>>(w, cfg.full_fan);
     if (ev) cudaEventRecord(ev[3], s);
@@ -1327,6 +1334,7 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     cfg.full_fan = (opt && (opt->flags & PCH_FLAG_FULL_FAN)) ? 1 : 0;
     cfg.profile = (opt && (opt->flags & PCH_FLAG_PROFILE)) ? 1 : 0;
     cfg.hops = (opt && opt->hops > 0) ? opt->hops : default_hops();
+    cfg.tail_cut = default_tail_cut();
     cfg.unroll = 2;
     int bits = 1;
     while ((1LL << bits) <= total_keys) ++bits;   // invalid key ~0u must exceed all valid keys

@@ -22,6 +22,7 @@ struct SolveCfg {
     int full_fan;
     int profile;
     int hops;
+    int tail_cut;           // stop chaining once the selected list is dry and fewer entries are queued
     const float* mlp;
 };
 
@@ -30,6 +31,7 @@ enum { kOutHost = 0, kOutDevice = 1, kOutNone = 2 };
 long long default_k();
 int default_hops();
 int default_prop_blocks_per_sm(int block);
+int default_tail_cut();
 const float* mlp_device_params();
 
 pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* srcs, int n_src,
