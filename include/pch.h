@@ -60,7 +60,12 @@ enum {
     PCH_CONTROL_PLAIN = 0,    /* fixed window count k per iteration (the paper's k) */
     PCH_CONTROL_LEARNED = 1,  /* MLP controller maps frontier statistics to the threshold;
                                  falls back to PLAIN on a non-finite or out-of-range output */
-    PCH_CONTROL_STRIDED = 2   /* the paper's approximate k-selection of Section 5.1 */
+    PCH_CONTROL_STRIDED = 2   /* the paper's approximate k-selection of Section 5.1: T threads
+                                 each take every T-th pending window and select their
+                                 ceil(k / T) nearest, about k windows per instance in total.
+                                 T is 2048 threads per SM; the per-thread count is rounded up
+                                 to a power of two (at most 16, T grows beyond that).  Each
+                                 selected window propagates one hop (hops is ignored) */
 };
 
 /* Iteration driver. */

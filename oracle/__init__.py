@@ -2,7 +2,7 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
 import this package.  It wraps ``ich_oracle.cpp`` (sequential FP64 Chen-Han/Xin-Wang,
-Algorithm 2 of the paper) and ``mlp_oracle.py`` (FP64 reference of the selection
+Algorithm 2 of the paper, and the sequential CPU PCH variant of Section 6) and ``mlp_oracle.py`` (FP64 reference of the selection
 controller's network).  It shares no code with the CUDA path.
 """
 from __future__ import annotations
@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
-ORDER_PQ, ORDER_FIFO, ORDER_RANDOM = 0, 1, 2
+ORDER_PQ, ORDER_FIFO, ORDER_RANDOM, ORDER_BATCH = 0, 1, 2, 3
 NO_CH, NO_ICH = 4, 8
 
 
@@ -42,6 +42,9 @@ def _declare(lib):
         ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
         ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
         ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    lib.oracle_cpu_pch.restype = ctypes.c_int
+    lib.oracle_cpu_pch.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+                                   ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.oracle_vertex_angles.restype = ctypes.c_int
     lib.oracle_vertex_angles.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p]
@@ -71,7 +74,7 @@ def geodesic(vertices, faces, source=None, *, face=None, bary=None, sources=None
     v = np.ascontiguousarray(vertices, dtype=np.float64)
     f = np.ascontiguousarray(faces, dtype=np.int32)
     out = np.empty(v.shape[0], dtype=np.float64)
-    stats = np.zeros(4, dtype=np.int64)
+    stats = np.zeros(5, dtype=np.int64)
     b = np.zeros(3, dtype=np.float64)
     srcs = np.zeros(1, dtype=np.int32)
     if sources is not None:
@@ -89,8 +92,28 @@ def geodesic(vertices, faces, source=None, *, face=None, bary=None, sources=None
                              int(max_windows), nt, t.ctypes.data, out.ctypes.data, stats.ctypes.data)
     if rc != 0:
         raise OracleError(f"oracle_geodesic failed with code {rc}")
-    return out, {"created": int(stats[0]), "propagated": int(stats[1]), "peak": int(stats[2]),
-                 "events": int(stats[3])}
+    return out, _stats(stats)
+
+
+def _stats(stats):
+    return {"created": int(stats[0]), "propagated": int(stats[1]), "peak": int(stats[2]),
+            "events": int(stats[3]), "rounds": int(stats[4])}
+
+
+def cpu_pch(vertices, faces, source: int, k: int, *, flags: int = 0, lib=None):
+    """The CPU PCH algorithm of Section 6 (a sequential baseline of the parallel method):
+    rounds of the k nearest pending windows chosen by quickselect and propagated one by
+    one in no particular order.  Returns (dist[V], stats dict with "rounds")."""
+    lib = lib or _load()
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    f = np.ascontiguousarray(faces, dtype=np.int32)
+    out = np.empty(v.shape[0], dtype=np.float64)
+    stats = np.zeros(5, dtype=np.int64)
+    rc = lib.oracle_cpu_pch(v.shape[0], v.ctypes.data, f.shape[0], f.ctypes.data, int(source), int(k), int(flags),
+                            out.ctypes.data, stats.ctypes.data)
+    if rc != 0:
+        raise OracleError(f"oracle_cpu_pch failed with code {rc}")
+    return out, _stats(stats)
 
 
 def vertex_angles(vertices, faces):

@@ -41,7 +41,9 @@ const double kEpsTiny = 1e-12;
 const double kDomRel = 1e-12;
 
 enum {
-    ORDER_PQ = 0, ORDER_FIFO = 1, ORDER_RANDOM = 2, ORDER_MASK = 3,
+    ORDER_PQ = 0, ORDER_FIFO = 1, ORDER_RANDOM = 2,
+    ORDER_BATCH = 3,   // CPU PCH (Section 6): rounds of the k nearest windows, unordered
+    ORDER_MASK = 3,
     NO_CH = 4,       // disable "one angle one split"
     NO_ICH = 8,      // disable the Xin-Wang filter
 };
@@ -163,6 +165,11 @@ struct Solver {
     uint64_t seq = 0, rng = 0x9E3779B97F4A7C15ull;
     long long created = 0, propagated = 0, peak = 0, events = 0;
     long long max_windows;
+    // ORDER_BATCH: the pending pool and the current round's selection
+    long long batch_k = 1;
+    std::vector<Entry> pool, batch;
+    size_t bpos = 0;
+    long long rounds = 0;
 
     Solver(Mesh& mm, int fl, long long cap) : m(mm), flags(fl), max_windows(cap) {
         g.assign(m.nv, kInf);
@@ -170,7 +177,11 @@ struct Solver {
         aX.assign(3 * m.nf, 0.0);
     }
 
-    size_t qsize() const { return (flags & ORDER_MASK) == ORDER_PQ ? pq.size() : fifo.size(); }
+    size_t qsize() const {
+        const int order = flags & ORDER_MASK;
+        if (order == ORDER_BATCH) return pool.size() + (batch.size() - bpos);
+        return order == ORDER_PQ ? pq.size() : fifo.size();
+    }
 
     double cap = kInf;   // NO_ICH only: drop windows beyond every vertex's edge-path distance
 
@@ -181,6 +192,8 @@ struct Solver {
         int order = flags & ORDER_MASK;
         if (order == ORDER_PQ) {
             pq.push(en);
+        } else if (order == ORDER_BATCH) {
+            pool.push_back(en);
         } else if (order == ORDER_FIFO) {
             fifo.push_back(en);
         } else {   // seeded random order: insert at the front or the back
@@ -195,6 +208,29 @@ struct Solver {
         if ((flags & ORDER_MASK) == ORDER_PQ) {
             if (pq.empty()) return false;
             out = pq.top(); pq.pop(); return true;
+        }
+        if ((flags & ORDER_MASK) == ORDER_BATCH) {
+            // Section 6, "The PCH algorithm on the CPU": each round takes the k windows
+            // nearest the source by quickselect, without ordering them, and propagates
+            // them one by one; windows created meanwhile wait for the next round.
+            if (bpos == batch.size()) {
+                batch.clear();
+                bpos = 0;
+                if (pool.empty()) return false;
+                if ((long long)pool.size() > batch_k) {
+                    std::nth_element(pool.begin(), pool.begin() + batch_k, pool.end(),
+                                     [](const Entry& a, const Entry& b) {
+                                         return a.key != b.key ? a.key < b.key : a.seq < b.seq;
+                                     });
+                    batch.assign(pool.begin(), pool.begin() + batch_k);
+                    pool.erase(pool.begin(), pool.begin() + batch_k);
+                } else {
+                    batch.swap(pool);
+                }
+                ++rounds;
+            }
+            out = batch[bpos++];
+            return true;
         }
         if (fifo.empty()) return false;
         out = fifo.front(); fifo.pop_front(); return true;
@@ -400,25 +436,16 @@ struct Solver {
 
 }  // namespace
 
-extern "C" {
-
-// Exact geodesic distance from one source to every vertex.
-//  src_kind 0: vertex source `src_vertex`; 1: point in face `src_face` with barycentric
-//  `src_bary[3]`; 2: `n_src` vertex sources `srcs` (distance to the nearest one,
-//  Section 4.2's source set S).
-//  flags: ORDER_* | NO_CH | NO_ICH.  targets/n_targets: stop once those vertices are
-//  final (other entries of out are then upper bounds).  stats[0..3] = windows created,
-//  windows propagated, peak queue, distance events.
-// Returns 0, or <0 on invalid / non-manifold / degenerate input or window cap exceeded.
-int oracle_geodesic(int nv, const double* xyz, int nf, const int* tri, int src_kind, int src_vertex,
-                    int src_face, const double* src_bary, int n_src, const int* srcs, int flags,
-                    long long max_windows, int n_targets, const int* targets, double* out,
-                    long long* stats) {
+static int solve_field(int nv, const double* xyz, int nf, const int* tri, int src_kind, int src_vertex,
+                       int src_face, const double* src_bary, int n_src, const int* srcs, int flags,
+                       long long max_windows, int n_targets, const int* targets, double* out,
+                       long long* stats, long long batch_k) {
     Mesh m;
     m.nv = nv; m.nf = nf; m.xyz = xyz; m.tri = tri;
     int rc = build_mesh(m);
     if (rc != 0) return rc;
     Solver s(m, flags, max_windows > 0 ? max_windows : (1LL << 40));
+    s.batch_k = batch_k > 0 ? batch_k : 1;
     std::vector<std::pair<int, double>> work;
     if (src_kind == 0 || src_kind == 2) {
         // Algorithm 1: geod_dist = 0 at the sources; a window on every edge opposite them.
@@ -481,8 +508,39 @@ int oracle_geodesic(int nv, const double* xyz, int nf, const int* tri, int src_k
     for (int v = 0; v < nv; ++v) out[v] = s.g[v];
     if (stats) {
         stats[0] = s.created; stats[1] = s.propagated; stats[2] = s.peak; stats[3] = s.events;
+        stats[4] = s.rounds;
     }
     return rc;
+}
+
+extern "C" {
+
+// Exact geodesic distance from one source to every vertex.
+//  src_kind 0: vertex source `src_vertex`; 1: point in face `src_face` with barycentric
+//  `src_bary[3]`; 2: `n_src` vertex sources `srcs` (distance to the nearest one,
+//  Section 4.2's source set S).
+//  flags: ORDER_* | NO_CH | NO_ICH (ORDER_BATCH takes one window per round here; see
+//  oracle_cpu_pch).  targets/n_targets: stop once those vertices are final (other
+//  entries of out are then upper bounds; the priority-queue order only).
+//  stats[0..4] = windows created, windows propagated, peak queue, distance events, rounds.
+// Returns 0, or <0 on invalid / non-manifold / degenerate input or window cap exceeded.
+int oracle_geodesic(int nv, const double* xyz, int nf, const int* tri, int src_kind, int src_vertex,
+                    int src_face, const double* src_bary, int n_src, const int* srcs, int flags,
+                    long long max_windows, int n_targets, const int* targets, double* out,
+                    long long* stats) {
+    return solve_field(nv, xyz, nf, tri, src_kind, src_vertex, src_face, src_bary, n_src, srcs, flags,
+                       max_windows, n_targets, targets, out, stats, 1);
+}
+
+// The CPU PCH algorithm of Section 6: the same propagation with the selection of
+// Algorithm 1 done sequentially, k windows a round (quickselect, not ordered), events
+// applied as they arise (sequential code has no conflicting writers).  flags: NO_CH |
+// NO_ICH; the order is ORDER_BATCH.  Same outputs and stats as oracle_geodesic.
+int oracle_cpu_pch(int nv, const double* xyz, int nf, const int* tri, int src_vertex, long long k, int flags,
+                   double* out, long long* stats) {
+    if (k < 1) return -1;
+    return solve_field(nv, xyz, nf, tri, 0, src_vertex, 0, nullptr, 0, nullptr,
+                       (flags & ~ORDER_MASK) | ORDER_BATCH, 0, 0, nullptr, out, stats, k);
 }
 
 // Total angle at every vertex and the pseudo-source flag the oracle uses (for tests).

@@ -221,29 +221,48 @@ __global__ void k_rec_ids(int nh, const int* __restrict__ twin, const unsigned c
     }
 }
 
-// Deterministic mean edge length and counts (single block, fixed order).
-__global__ void k_stats(int nh, int nv, const HERec* rec, const int* twin, const unsigned char* vflag, double* out_lsum,
-                        int* out_counts) {
+// Deterministic mean edge length and counts: block b reduces a fixed contiguous range of
+// half-edges and vertices in a fixed order, then k_stats_final adds the kStatBlocks
+// partial results in a fixed tree, so the sum does not depend on scheduling.
+constexpr int kStatBlocks = 256;
+
+__device__ __forceinline__ void block_sum3(double& s, int& a, int& b) {
     __shared__ double sh[256];
-    __shared__ int sb[256], sp[256];
-    double s = 0.0;
-    int nb = 0, np = 0;
-    for (int h = threadIdx.x; h < nh; h += blockDim.x) {
-        s += rec[h].L;
-        nb += twin[h] < 0;
-    }
-    for (int v = threadIdx.x; v < nv; v += blockDim.x) np += (vflag[v] & 2) ? 1 : 0;
-    sh[threadIdx.x] = s; sb[threadIdx.x] = nb; sp[threadIdx.x] = np;
+    __shared__ int sa[256], sb[256];
+    sh[threadIdx.x] = s; sa[threadIdx.x] = a; sb[threadIdx.x] = b;
     __syncthreads();
     for (int off = 128; off > 0; off >>= 1) {
         if (threadIdx.x < off) {
             sh[threadIdx.x] += sh[threadIdx.x + off];
+            sa[threadIdx.x] += sa[threadIdx.x + off];
             sb[threadIdx.x] += sb[threadIdx.x + off];
-            sp[threadIdx.x] += sp[threadIdx.x + off];
         }
         __syncthreads();
     }
-    if (threadIdx.x == 0) { *out_lsum = sh[0]; out_counts[0] = sb[0]; out_counts[1] = sp[0]; }
+    s = sh[0]; a = sa[0]; b = sb[0];
+}
+
+__global__ void __launch_bounds__(256) k_stats(int nh, int nv, const HERec* rec, const int* twin,
+                                               const unsigned char* vflag, double* part_l, int* part_c) {
+    const long long h0 = (long long)nh * blockIdx.x / gridDim.x, h1 = (long long)nh * (blockIdx.x + 1) / gridDim.x;
+    const long long v0 = (long long)nv * blockIdx.x / gridDim.x, v1 = (long long)nv * (blockIdx.x + 1) / gridDim.x;
+    double s = 0.0;
+    int nb = 0, np = 0;
+    for (long long h = h0 + threadIdx.x; h < h1; h += blockDim.x) {
+        s += rec[h].L;
+        nb += twin[h] < 0;
+    }
+    for (long long v = v0 + threadIdx.x; v < v1; v += blockDim.x) np += (vflag[v] & 2) ? 1 : 0;
+    block_sum3(s, nb, np);
+    if (threadIdx.x == 0) { part_l[blockIdx.x] = s; part_c[2 * blockIdx.x] = nb; part_c[2 * blockIdx.x + 1] = np; }
+}
+
+__global__ void __launch_bounds__(256) k_stats_final(const double* part_l, const int* part_c, double* out_lsum,
+                                                     int* out_counts) {
+    double s = part_l[threadIdx.x];
+    int nb = part_c[2 * threadIdx.x], np = part_c[2 * threadIdx.x + 1];
+    block_sum3(s, nb, np);
+    if (threadIdx.x == 0) { *out_lsum = s; out_counts[0] = nb; out_counts[1] = np; }
 }
 
 static void free_mesh(DevMesh& d) {
@@ -310,8 +329,8 @@ extern "C" pch_status pch_create_mesh(const double* vertices, int32_t n_vertices
         MCHK(cudaMalloc(&vcount, sizeof(int) * (nv + 1)));
         MCHK(cudaMalloc(&vout, sizeof(int) * nv));
         MCHK(cudaMalloc(&err, sizeof(int)));
-        MCHK(cudaMalloc(&counts, sizeof(int) * 2));
-        MCHK(cudaMalloc(&lsum, sizeof(double)));
+        MCHK(cudaMalloc(&counts, sizeof(int) * (2 + 2 * kStatBlocks)));
+        MCHK(cudaMalloc(&lsum, sizeof(double) * (1 + kStatBlocks)));
         MCHK(cudaMalloc(&scan_tmp, sizeof(int) * scan_tmp_ints(nv + 1)));
         MCHK(cudaMalloc(&hkeys, sizeof(unsigned long long) * cap));
         MCHK(cudaMalloc(&hvals, sizeof(int) * cap));
@@ -331,7 +350,8 @@ extern "C" pch_status pch_create_mesh(const double* vertices, int32_t n_vertices
         MCHK(exclusive_scan(vcount, d.vstart, nv + 1, scan_tmp, 0));
         k_rings<<<gv, tb>>>(nv, twin, vout, d.vstart, d.hang, d.vlist, d.vphi, d.vtheta, d.vflag, err);
         k_rec_ids<<<gb, tb>>>(nh, twin, d.vflag, d.rec);
-        k_stats<<<1, 256>>>(nh, nv, d.rec, twin, d.vflag, lsum, counts);
+        k_stats<<<kStatBlocks, 256>>>(nh, nv, d.rec, twin, d.vflag, lsum + 1, counts + 2);
+        k_stats_final<<<1, kStatBlocks>>>(lsum + 1, counts + 2, lsum, counts);
         MCHK(cudaGetLastError());
         MCHK(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
         MCHK(cudaMemcpy(&hl, lsum, sizeof(double), cudaMemcpyDeviceToHost));

@@ -157,6 +157,12 @@ struct Work {
     float* trace;           // controller trace rows
     int trace_cap;
     int* trace_rows;
+    // strided approximate selection (Section 5.1): stride_T > 0 virtual threads, thread t
+    // owns pool positions t, t + T, t + 2T, ... and selects its m nearest windows; the
+    // m-th nearest (key bits, position) of each thread is its threshold
+    int stride_T;
+    unsigned long long* sthr_key;
+    int* sthr_idx;
 };
 
 // Ordered u64 image of a nonnegative double (atomicMin-able, Section 4.2 Step 4).

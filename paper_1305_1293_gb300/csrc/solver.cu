@@ -299,7 +299,9 @@ __global__ void k_tau(Work w, int control, const float* __restrict__ mlp) {
                     f[kFeatures + 1] = (float)inst;
                 }
             }
-            c.tau = tau;
+            // the strided selection decides by per-thread thresholds instead; tau = -inf
+            // also turns chaining off (the paper propagates each selected window one hop)
+            c.tau = control == PCH_CONTROL_STRIDED ? -INFINITY : tau;
             c.n_pending = np;
             c.n_next = 0;
             if (c.kmin != ~0ull) c.ref = bitsd(c.kmin);   // min key of the current pool
@@ -307,6 +309,44 @@ __global__ void k_tau(Work w, int control, const float* __restrict__ mlp) {
         }
         for (int b = threadIdx.x; b < kBins; b += blockDim.x) hist_nx[inst * kBins + b] = 0u;
         __syncthreads();
+    }
+}
+
+// Section 5.1's approximate k-selection: virtual thread t of T scans the pool positions
+// t, t + T, t + 2T, ... and keeps its M nearest windows (by key, ties to the earlier
+// position); the M-th of them is the thread's threshold (all ones when it owns fewer than
+// M windows: it selects all of them).  k_compact then selects position i when
+// (key bits, i) <= the threshold of thread i mod T, so T * M windows are selected in
+// total (every window when the pool holds fewer).  The scan is coalesced: neighbouring
+// threads read neighbouring positions.
+template <int M>
+__global__ void __launch_bounds__(256) k_strided(Work w) {
+    Counters* cnt = w.cnt;
+    if (cnt->halt) return;
+    const int T = w.stride_T;
+    const double* __restrict__ key = w.pool[cnt->iter & 1].key;
+    const int n = min(cnt->n_pending, w.pool_cap);
+    for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+        unsigned long long bk[M];
+        int bi[M];
+#pragma unroll
+        for (int j = 0; j < M; ++j) { bk[j] = ~0ull; bi[j] = 0x7fffffff; }
+        for (int i = t; i < n; i += T) {
+            const unsigned long long kb = dbits(__ldcs(key + i));
+            if (kb < bk[M - 1]) {      // positions increase: an equal key keeps the earlier one
+                bk[M - 1] = kb;
+                bi[M - 1] = i;
+#pragma unroll
+                for (int j = M - 1; j > 0; --j) {
+                    if (bk[j] < bk[j - 1]) {
+                        const unsigned long long tk = bk[j]; bk[j] = bk[j - 1]; bk[j - 1] = tk;
+                        const int ti = bi[j]; bi[j] = bi[j - 1]; bi[j - 1] = ti;
+                    }
+                }
+            }
+        }
+        w.sthr_key[t] = bk[M - 1];
+        w.sthr_idx[t] = bi[M - 1];
     }
 }
 
@@ -332,7 +372,14 @@ __global__ void __launch_bounds__(256) k_compact(Work w) {
             load_win(cur, i, he, inst, d, A, B, px, py, key, src, IA, IB);
             if (stale_source(w.inst[inst], src, d)) valid = false;   // dropped from the pool
         }
-        bool sel = valid && key <= w.ctl[inst].tau;
+        bool sel;
+        if (w.stride_T > 0) {           // strided selection: the owning thread's threshold
+            const int t = i % w.stride_T;
+            const unsigned long long kb = dbits(key), tk = w.sthr_key[t];
+            sel = valid && (kb < tk || (kb == tk && i <= w.sthr_idx[t]));
+        } else {
+            sel = valid && key <= w.ctl[inst].tau;
+        }
         int slot = warp_reserve(&cnt->n_sel, sel ? 1 : 0);
         if (sel && slot >= w.sel_cap) sel = false;   // work list full: stays pending
         if (sel) store_win(w.sel, slot, he, inst, d, A, B, px, py, key, src, IA, IB);
@@ -978,6 +1025,8 @@ struct Workspace {
     Alloc pools;            // pools, arena, sort buffers, requests (sized by caps)
     Alloc inst_mem;         // g / angle_split / stamps (sized by the instances)
     Alloc fixed;            // counters, tables
+    Alloc sthr;             // strided-selection thresholds (PCH_CONTROL_STRIDED)
+    int sthr_cap = 0;
     Work w{};
     int pool_cap = 0, sel_cap = 0, arena_cap = 0, req_cap = 0;
     long long g_cap = 0, ang_cap = 0, st_cap = 0;
@@ -1004,6 +1053,7 @@ void destroy_workspace(Workspace* ws) {
     ws->pools.release();
     ws->inst_mem.release();
     ws->fixed.release();
+    ws->sthr.release();
     if (ws->cnt_host) cudaFreeHost(ws->cnt_host);
     for (auto& e : ws->ev) if (e) cudaEventDestroy(e);
     delete ws;
@@ -1031,14 +1081,20 @@ static cudaError_t alloc_soa(Alloc& a, WinSoA& s, int cap) {
     return a.get(&s.src, cap);
 }
 
-static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap) {
+// Capacities: the work list holds sel_cap windows (more selected windows simply stay
+// pending), the child arena 6 * sel_cap (two children per selected window plus the half
+// that chaining may fill, so it cannot overflow), the pending pools at least twice the
+// arena (the loop halts for the host to grow them before they could overflow), and the
+// fan requests req_cap (an overflow fails the attempt; the solve is then re-run with
+// twice the room).
+static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap, int req_min = 0) {
     int arena_cap = 6 * sel_cap;
     if (pool_cap < 2 * arena_cap) pool_cap = 2 * arena_cap;
-    if (sel_cap <= ws->sel_cap && pool_cap <= ws->pool_cap) return PCH_OK;
+    if (sel_cap <= ws->sel_cap && pool_cap <= ws->pool_cap && req_min <= ws->req_cap) return PCH_OK;
     sel_cap = std::max(sel_cap, ws->sel_cap);
     pool_cap = std::max(pool_cap, ws->pool_cap);
     arena_cap = 6 * sel_cap;
-    const int req_cap = 4 * sel_cap + (1 << 20);
+    const int req_cap = std::max({4 * sel_cap + (1 << 20), req_min, ws->req_cap});
     const int sort_blocks = 2 * sm_count();
     drop_graph(ws);
     Work& w = ws->w;
@@ -1153,7 +1209,7 @@ static int grid_for(int blocks_per_sm) { return sm_count() * blocks_per_sm; }
 // Kernels one iteration launches (for pch_stats.kernel_launches).
 static int kernels_per_iteration(const SolveCfg& cfg) {
     int passes = (cfg.key_bits + kRsDigitBits - 1) / kRsDigitBits;
-    return 6 + sort_kernels_per_pass() * (passes < 1 ? 1 : passes);
+    return 6 + (cfg.stride_T > 0 ? 1 : 0) + sort_kernels_per_pass() * (passes < 1 ? 1 : passes);
 }
 
 // Launch one iteration (all phases).  With `ev` (7 events) the phase boundaries are
@@ -1164,6 +1220,16 @@ static cudaError_t launch_iteration(Workspace* ws, cudaStream_t s, const SolveCf
     const int tpb = 256;
     if (ev) cudaEventRecord(ev[0], s);
     k_tau<<<std::min(w.n_inst, 1024), 256, 0, s>>>(w, cfg.control, cfg.mlp);
+    if (cfg.stride_T > 0) {
+        const int g = std::min((cfg.stride_T + 255) / 256, grid_for(8));
+        switch (cfg.stride_m) {
+            case 1: k_strided<1><<<g, 256, 0, s>>>(w); break;
+            case 2: k_strided<2><<<g, 256, 0, s>>>(w); break;
+            case 4: k_strided<4><<<g, 256, 0, s>>>(w); break;
+            case 8: k_strided<8><<<g, 256, 0, s>>>(w); break;
+            default: k_strided<16><<<g, 256, 0, s>>>(w); break;
+        }
+    }
     k_compact<<<grid_for(4), tpb, 0, s>>>(w);
     if (ev) cudaEventRecord(ev[1], s);
     k_propagate<<<grid_for(cfg.prop_blocks_per_sm), cfg.prop_threads, cfg.prop_threads * kPropQueueBytesPerThread, s>>>(
@@ -1299,7 +1365,7 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         stats->windows_propagated = (int64_t)c.propagated;
         stats->peak_pending = (int64_t)c.peak_pending;
         stats->ms_total = ms;
-        stats->bytes_workspace = (int64_t)(ws->pools.bytes + ws->inst_mem.bytes + ws->fixed.bytes);
+        stats->bytes_workspace = (int64_t)(ws->pools.bytes + ws->inst_mem.bytes + ws->fixed.bytes + ws->sthr.bytes);
         stats->kernel_launches += launches;
         stats->fans = (int64_t)c.fans;
         stats->fan_windows = (int64_t)c.fan_windows;
@@ -1340,7 +1406,21 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     while ((1LL << bits) <= total_keys) ++bits;   // invalid key ~0u must exceed all valid keys
     cfg.key_bits = bits;
     cfg.mlp = nullptr;
-    (void)n_inst;
+    cfg.stride_T = cfg.stride_m = 0;
+    if (cfg.control == PCH_CONTROL_STRIDED) {
+        // Section 5.1: T threads each select their ceil(k / T) nearest windows.  T is the
+        // number of threads the GPU holds at once (2048 per SM); each selects M of them, M
+        // rounded up to a power of two (at most 16, beyond which T grows instead), and
+        // T = ceil(K / M) for K = k windows per instance.
+        const long long K = std::max<long long>(1, cfg.k * (long long)n_inst);
+        const long long Tmax = (long long)sm_count() * 2048;
+        long long m = (K + Tmax - 1) / Tmax;
+        int M = 1;
+        while (M < m && M < 16) M <<= 1;
+        long long T = (K + M - 1) / M;
+        cfg.stride_m = M;
+        cfg.stride_T = (int)std::min<long long>(T, 1LL << 30);
+    }
     return cfg;
 }
 
@@ -1370,6 +1450,8 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
     if (opt && opt->block != 0 && (opt->block < 32 || opt->block > 256 || opt->block % 32 != 0))
         return set_error(PCH_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 256], got %d", opt->block);
     if (opt && opt->k < 0) return set_error(PCH_ERR_INVALID_ARG, "k must be >= 0");
+    if (opt && (opt->control < PCH_CONTROL_PLAIN || opt->control > PCH_CONTROL_STRIDED))
+        return set_error(PCH_ERR_INVALID_ARG, "unknown control %d", opt->control);
     cudaStream_t s = opt ? (cudaStream_t)opt->stream : (cudaStream_t)0;
     Workspace* ws;
     pch_status st = ensure_workspace(meshes[0], &ws);
@@ -1408,13 +1490,28 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
         c.k_target = cfg.k;
         c.active = 1;
     }
+    // the work list never needs more than the pending windows, which rarely exceed the
+    // half-edge count; a larger k only leaves the rest pending
     long long sel_want = std::max<long long>(65536, 4LL * cfg.k * std::min(n_inst, 64));
+    sel_want = std::min<long long>(sel_want, std::max<long long>(65536, aoff));
     sel_want = std::min<long long>(sel_want, 1 << 24);
     int pool_want = (int)std::min<long long>(std::max<long long>(2 * 6 * sel_want, 1 << 20), (1LL << 30));
     st = ensure_pools(ws, (int)sel_want, pool_want);
     if (st != PCH_OK) return st;
     Work& w = ws->w;
     w.n_inst = n_inst;
+    if (cfg.stride_T > ws->sthr_cap) {
+        drop_graph(ws);
+        ws->sthr.release();
+        ws->sthr_cap = 0;
+        if (ws->sthr.get(&w.sthr_key, (size_t)cfg.stride_T) != cudaSuccess ||
+            ws->sthr.get(&w.sthr_idx, (size_t)cfg.stride_T) != cudaSuccess) {
+            ws->sthr.release();
+            return set_error(PCH_ERR_OOM, "strided selection thresholds: allocation failed");
+        }
+        ws->sthr_cap = cfg.stride_T;
+    }
+    w.stride_T = cfg.stride_T;
     ws->trace_on = opt && (opt->flags & PCH_FLAG_TRACE);
     if (ws->trace_on && !ws->trace_buf) {
         ws->trace_cap = 1 << 18;
@@ -1426,27 +1523,38 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
     w.trace_cap = ws->trace_cap;
     w.trace_rows = ws->trace_rows;
     if (cfg.control == PCH_CONTROL_LEARNED) cfg.mlp = mlp_device_params();
-    // upload tables, clear state
-    PCH_CUDA(cudaMemcpyAsync(w.inst, hinst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice, s));
-    PCH_CUDA(cudaMemcpyAsync(w.ctl, hctl.data(), sizeof(InstCtl) * n_inst, cudaMemcpyHostToDevice, s));
-    PCH_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(Counters), s));
-    PCH_CUDA(cudaMemsetAsync(w.hist[0], 0, sizeof(unsigned) * kBins * n_inst, s));
-    PCH_CUDA(cudaMemsetAsync(w.hist[1], 0, sizeof(unsigned) * kBins * n_inst, s));
-    PCH_CUDA(cudaMemsetAsync(ws->ang_all, 0xff, sizeof(unsigned long long) * aoff, s));
-    PCH_CUDA(cudaMemsetAsync(ws->stamp_all, 0, sizeof(unsigned) * goff, s));
-    if (w.trace_rows) PCH_CUDA(cudaMemsetAsync(w.trace_rows, 0, sizeof(int), s));
-    if (stats) std::memset(stats, 0, sizeof(pch_stats));
-    k_fill_inf<<<grid_for(4), 256, 0, s>>>(ws->g_all, goff);
-    SrcDev* dsrc = nullptr;
-    PCH_CUDA(cudaMallocAsync(&dsrc, sizeof(SrcDev) * n_src, s));
-    PCH_CUDA(cudaMemcpyAsync(dsrc, srcs, sizeof(SrcDev) * n_src, cudaMemcpyHostToDevice, s));
-    k_init_sources<<<(n_src + 127) / 128, 128, 0, s>>>(w, dsrc, n_src);
-    k_init_face_sources<<<(n_src + 127) / 128, 128, 0, s>>>(w, dsrc, n_src);
-    PCH_CUDA(cudaGetLastError());
-    PCH_CUDA(cudaFreeAsync(dsrc, s));
-    if (stats) stats->kernel_launches = 3;
-    st = run_solve(ws, s, cfg, stats);
-    if (st != PCH_OK) return st;
+    // a fan-request overflow fails the attempt (a lost request would lose a fan); the
+    // solve is then run again from the start with twice the request room
+    for (int attempt = 0;; ++attempt) {
+        // upload tables, clear state
+        PCH_CUDA(cudaMemcpyAsync(w.inst, hinst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice, s));
+        PCH_CUDA(cudaMemcpyAsync(w.ctl, hctl.data(), sizeof(InstCtl) * n_inst, cudaMemcpyHostToDevice, s));
+        PCH_CUDA(cudaMemsetAsync(w.cnt, 0, sizeof(Counters), s));
+        PCH_CUDA(cudaMemsetAsync(w.hist[0], 0, sizeof(unsigned) * kBins * n_inst, s));
+        PCH_CUDA(cudaMemsetAsync(w.hist[1], 0, sizeof(unsigned) * kBins * n_inst, s));
+        PCH_CUDA(cudaMemsetAsync(ws->ang_all, 0xff, sizeof(unsigned long long) * aoff, s));
+        PCH_CUDA(cudaMemsetAsync(ws->stamp_all, 0, sizeof(unsigned) * goff, s));
+        if (w.trace_rows) PCH_CUDA(cudaMemsetAsync(w.trace_rows, 0, sizeof(int), s));
+        if (stats) std::memset(stats, 0, sizeof(pch_stats));
+        k_fill_inf<<<grid_for(4), 256, 0, s>>>(ws->g_all, goff);
+        SrcDev* dsrc = nullptr;
+        PCH_CUDA(cudaMallocAsync(&dsrc, sizeof(SrcDev) * n_src, s));
+        PCH_CUDA(cudaMemcpyAsync(dsrc, srcs, sizeof(SrcDev) * n_src, cudaMemcpyHostToDevice, s));
+        k_init_sources<<<(n_src + 127) / 128, 128, 0, s>>>(w, dsrc, n_src);
+        k_init_face_sources<<<(n_src + 127) / 128, 128, 0, s>>>(w, dsrc, n_src);
+        PCH_CUDA(cudaGetLastError());
+        PCH_CUDA(cudaFreeAsync(dsrc, s));
+        if (stats) stats->kernel_launches = 3;
+        st = run_solve(ws, s, cfg, stats);
+        if (st == PCH_ERR_CAPACITY && (ws->cnt_host->error & kErrReqFull) && attempt < 4) {
+            st = ensure_pools(ws, ws->sel_cap, ws->pool_cap, 2 * ws->req_cap);
+            if (st != PCH_OK) return st;
+            clear_error();
+            continue;
+        }
+        if (st != PCH_OK) return st;
+        break;
+    }
     // results
     for (int i = 0; i < n_inst; ++i) {
         const DevMesh& dm = meshes[i]->dm;

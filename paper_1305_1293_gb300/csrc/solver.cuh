@@ -23,6 +23,8 @@ struct SolveCfg {
     int profile;
     int hops;
     int tail_cut;           // stop chaining once the selected list is dry and fewer entries are queued
+    int stride_T;           // PCH_CONTROL_STRIDED: virtual threads of the strided selection (else 0)
+    int stride_m;           // PCH_CONTROL_STRIDED: windows each of them selects (1, 2, 4, 8 or 16)
     const float* mlp;
 };
 

@@ -95,6 +95,24 @@ def test_order_invariance_and_filter_soundness(oracle_lib, name, make):
     assert st["created"] <= fifo["created"]
 
 
+@pytest.mark.parametrize("name,make", SMALL[:3], ids=[t[0] for t in SMALL[:3]])
+def test_cpu_pch_rounds_exact(oracle_lib, name, make):
+    """Section 6's CPU PCH (rounds of the k nearest windows, quickselect, no order inside
+    a round) gives the same field as the priority queue (Remark 2); with k = 1 a round is
+    exactly one priority-queue pop, so it creates exactly the same windows; larger rounds
+    cost extra windows."""
+    m = make()
+    src = 5
+    ref, st = oracle_lib.geodesic(m.vertices, m.faces, src)
+    d1, s1 = oracle_lib.cpu_pch(m.vertices, m.faces, src, 1)
+    assert np.array_equal(d1, ref)
+    assert s1["created"] == st["created"] and s1["rounds"] == s1["created"]
+    for k in (7, 64, 1024):
+        d, sk = oracle_lib.cpu_pch(m.vertices, m.faces, src, k)
+        assert _rel(d, ref) < 1e-12, k
+        assert sk["created"] >= st["created"] and sk["rounds"] < s1["rounds"]
+
+
 def test_ich_filter_off_tiny(oracle_lib):
     """With the Xin-Wang filter off (CH rule only) the distances are unchanged."""
     for name, make in TINY[:5]:

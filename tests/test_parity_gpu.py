@@ -124,6 +124,39 @@ def test_result_independent_of_k_and_hops(pch, oracle_lib, k, hops):
         assert st["windows_chained"] == 0
 
 
+@pytest.mark.parametrize("k", [3, 256, 24576])
+def test_strided_selection_exact(pch, oracle_lib, k):
+    """Section 5.1's approximate k-selection (Remark 2): the selection is approximate,
+    the field is exact; every selected window propagates one hop."""
+    m = mg.terrain(24, 20, seed=31)
+    s = mg.terrain_center(24, 20)
+    ref, _ = oracle_lib.geodesic(m.vertices, m.faces, s)
+    got, st = gpu_solve(pch, m, s, k=k, control=pch.CONTROL_STRIDED, hops=8, max_iters=1 << 22)
+    assert max_rel(got, ref) < TOL
+    assert st["windows_chained"] == 0 and st["iterations"] > 1
+
+
+def test_strided_selection_batch_and_host_loop(pch, oracle_lib):
+    meshes, srcs = mg.workload("batch", "small")
+    hs = [pch.Mesh(m.vertices, m.faces) for m in meshes]
+    for loop in (pch.LOOP_GRAPH, pch.LOOP_HOST):
+        outs = pch.solve_batch(hs, [int(s[0]) for s in srcs], control=pch.CONTROL_STRIDED, k=4096, loop=loop)
+        for m, s, got in zip(meshes, srcs, outs):
+            ref, _ = oracle_lib.geodesic(m.vertices, m.faces, int(s[0]))
+            assert max_rel(got, ref) < TOL
+    for x in hs:
+        x.close()
+
+
+def test_unknown_control_rejected(pch):
+    m = mg.icosphere(1)
+    mesh = pch.Mesh(m.vertices, m.faces)
+    with pytest.raises(pch.PchError) as e:
+        pch.solve(mesh, 0, control=7)
+    assert e.value.status == pch.PCH_ERR_INVALID_ARG
+    mesh.close()
+
+
 @pytest.mark.parametrize("flags", ["NO_TRIM", "FULL_FAN", "NO_TRIM|FULL_FAN"])
 def test_variants_same_result(pch, oracle_lib, flags):
     """Trimming and the fanned-area restriction remove only useless windows."""
