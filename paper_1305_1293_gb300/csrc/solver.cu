@@ -64,12 +64,15 @@ __device__ __forceinline__ WarpScan warp_scan(int x) {
     return {incl - x, __shfl_sync(0xffffffffu, incl, 31)};
 }
 
-// Warp-aggregated reservation of `x` slots per lane on counter `c`; returns the lane's base.
-__device__ __forceinline__ int warp_reserve(int* c, int x) {
+// Warp-aggregated reservation of `x` slots per lane on counter `c`; returns the lane's
+// base.  With `fill`, a warp that reserved anything gets the counter's value after its
+// reservation there (unchanged otherwise).
+__device__ __forceinline__ int warp_reserve(int* c, int x, int* fill = nullptr) {
     WarpScan s = warp_scan(x);
     int base = 0;
     if ((threadIdx.x & 31) == 31 && s.total) base = atomicAdd(c, s.total);
     base = __shfl_sync(0xffffffffu, base, 31);
+    if (fill && s.total) *fill = base + s.total;
     return base + s.excl;
 }
 
@@ -561,6 +564,11 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
                 }
                 const bool rt = j == 0 && right;
                 ++ncomp;
+                {   // the child's record, needed when it is propagated (next round when chained)
+                    const char* cr = reinterpret_cast<const char*>(I.rec + (rt ? R.tw1 : R.tw2));
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(cr));
+                    asm volatile("prefetch.global.L1 [%0];" ::"l"(cr + sizeof(HERec) - 8));
+                }
                 // both sides as one select-driven path (a warp holds left and right children)
                 const double Lc = rt ? R.L1 : R.L2;
                 const double sc = rt ? R.iL1 : R.iL2;
@@ -650,6 +658,11 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
     int2* req = w.req[it & 1];
     double4* req_d = w.req_d[it & 1];
     const int room = w.arena_cap / 2 - 2 * (int)(gridDim.x * blockDim.x);
+    // the arena fill this warp last saw (updated whenever it reserves arena slots): a
+    // warp overshoots the room by at most one round of its own writes
+    int seen_child = *(volatile int*)&cnt->n_child;
+    // statistics, kept per thread and added to the counters once when the block ends
+    unsigned n_prop = 0, n_chain = 0, n_exam = 0, n_occ = 0, n_comp = 0;
     if (t == 0) {
         for (int i = 0; i < 3; ++i) s_nq[i] = s_dry[i] = 0;
     }
@@ -658,7 +671,15 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
         __syncthreads();   // last round's pushes and s_dry are visible; its reads are done
         const int nq = min(s_nq[r % 3], (int)blockDim.x);
         const bool dry = s_dry[r % 3] != 0;
-        if (nq == 0 && dry) break;                 // uniform over the block
+        if (nq == 0 && dry) {                      // uniform over the block
+            const unsigned sums[5] = {__reduce_add_sync(full, n_prop), __reduce_add_sync(full, n_chain),
+                                      __reduce_add_sync(full, n_exam), __reduce_add_sync(full, n_occ),
+                                      __reduce_add_sync(full, n_comp)};
+            unsigned long long* dst[5] = {&cnt->propagated, &cnt->chained, &cnt->examined, &cnt->occupied,
+                                          &cnt->children};
+            if (lane < 5 && sums[lane]) atomicAdd(dst[lane], (unsigned long long)sums[lane]);
+            break;
+        }
         if (t == 0) {
             s_nq[(r + 2) % 3] = 0;
             s_dry[(r + 2) % 3] = 0;
@@ -701,7 +722,7 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
             prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, task, hop, tq, c0, c1, nch, occ,
                                     ncomp, cIA, cIB);
         bool cont = have && nch > 0 && hop + 1 < hops && le_s(c0.key, w.ctl[inst].tau) &&
-                    (!dry || nq >= tail_cut) && *(volatile int*)&cnt->n_child < room;
+                    (!dry || nq >= tail_cut) && seen_child < room;
         // the continuing child goes to the queue while it has room, every other child to
         // the arena
         const int qs = warp_reserve(&s_nq[(r + 1) % 3], cont ? 1 : 0);
@@ -712,7 +733,9 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
             q_IA[wb * blockDim.x + qs] = c0.IA; q_IB[wb * blockDim.x + qs] = c0.IB;
         }
         const int nwrite = have ? (cont ? nch - 1 : nch) : 0;
-        const int slot = warp_reserve(&cnt->n_child, nwrite);
+        int fill = -1;
+        const int slot = warp_reserve(&cnt->n_child, nwrite, &fill);
+        if (fill >= 0) seen_child = fill;
         if (nwrite > 0) {
             const ChildOut& cf = cont ? c1 : c0;
             if (slot < w.arena_cap)
@@ -724,11 +747,11 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
                 store_win(w.arena, slot + 1, c1.he, inst, d, c1.A, c1.B, c1.px, c1.py, c1.key, src, c1.IA, c1.IB);
             else atomicOr(&cnt->error, kErrPoolFull);
         }
-        warp_add_ull(&cnt->propagated, prop ? 1 : 0);
-        warp_add_ull(&cnt->chained, cont ? 1 : 0);
-        warp_add_ull(&cnt->examined, have && !task ? 1 : 0);
-        warp_add_ull(&cnt->occupied, occ);
-        warp_add_ull(&cnt->children, ncomp);
+        n_prop += prop ? 1u : 0u;
+        n_chain += cont ? 1u : 0u;
+        n_exam += have && !task ? 1u : 0u;
+        n_occ += (unsigned)occ;
+        n_comp += (unsigned)ncomp;
     }
 }
 
