@@ -44,15 +44,15 @@ int default_tail_cut() {
     return 0;
 }
 
-// Resident propagation blocks per SM: 512 threads per SM (16 warps of 128 registers a
-// thread fill the register file), unless PCH_PROP_BLOCKS_PER_SM says otherwise.
+// Resident propagation blocks per SM: 384 threads per SM (12 warps of up to 168
+// registers a thread fill the register file), unless PCH_PROP_BLOCKS_PER_SM says otherwise.
 int default_prop_blocks_per_sm(int block) {
     const char* e = std::getenv("PCH_PROP_BLOCKS_PER_SM");
     if (e) {
         int v = std::atoi(e);
         if (v > 0 && v <= 32) return v;
     }
-    return block >= 512 ? 1 : 512 / block;
+    return block >= 384 ? 1 : 384 / block;
 }
 
 // ---------------------------------------------------------------- training kernels

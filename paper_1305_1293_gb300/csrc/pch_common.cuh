@@ -123,7 +123,7 @@ struct Counters {
     int halt;               // set by k_finish when the loop must stop; every kernel no-ops
     unsigned long long created, propagated, filtered, trimmed, peak_pending;
     unsigned long long fans, fan_windows, fan_cand, chained;
-    unsigned long long examined, occupied, children;   // propagation path counts (FP64 op tally)
+    unsigned long long examined, occupied, children, rays;   // propagation path counts (FP64 op tally)
     unsigned long long scanned, sorted;               // windows read by compaction / sorted
     int work_next;          // next work-list index handed to a propagation lane
     int pad2;

@@ -457,11 +457,13 @@ constexpr int kHopTask = 1 << 30;   // hop-field flag of a queue entry: a deferr
 __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, int2* req, double4* req_d, int inst,
                                                  int src, double d, int h, double A, double B, double px, double py,
                                                  bool task, int hop, const TaskQueue& q, ChildOut& c0, ChildOut& c1,
-                                                 int& nch, int& occ_out, int& ncomp, double IA_in, double IB_in) {
+                                                 int& nch, int& occ_out, int& ncomp, int& nray, double IA_in,
+                                                 double IB_in) {
     bool prop = false;
     nch = 0;
     occ_out = 0;
     ncomp = 0;
+    nray = 0;
     {
         const Inst& I = w.inst[inst];
         const HERec R = I.rec[h];
@@ -479,9 +481,13 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
         if (task) {
             occ = true;
             left = R.tw2 >= 0;
-        } else if (!(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)) || stale_source(I, src, d))) {
+        } else if ((hop > 0 || !(dominated(d + IB, g0 + B) || dominated(d + IA, g1 + (L - A)))) &&
+                   !stale_source(I, src, d)) {
             // Xin-Wang endpoint tests against the current distances passed: the window is
-            // useless if the path via v0 beats it at B, or the path via v1 at A
+            // useless if the path via v0 beats it at B, or the path via v1 at A.  A chained
+            // window (hop > 0) passed the same two tests when its parent created it a round
+            // ago; distances only fall, so repeating them could only prune more, never keep
+            // a window that must go, and they are skipped.
             prop = true;
             const double py2 = py * py;
             const double tol = kEpsSnap * L;
@@ -564,6 +570,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
                 }
                 const bool rt = j == 0 && right;
                 ++ncomp;
+                nray += occ ? 1 : 2;
                 {   // the child's record, needed when it is propagated (next round when chained)
                     const char* cr = reinterpret_cast<const char*>(I.rec + (rt ? R.tw1 : R.tw2));
                     asm volatile("prefetch.global.L1 [%0];" ::"l"(cr));
@@ -628,7 +635,8 @@ constexpr int kPropQueueBytesPerThread = 2 * (7 * 8 + 4 * 4);
 // (chaining stops while the child arena is half full).
 // Repacking the chains onto the lowest lanes every round keeps the warps that do issue
 // FP64 work full once the selected list runs dry, and leaves the other warps idle.
-__global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops, int tail_cut) {
+// 168 registers a thread at most (148 used, no spills): 6 blocks of 64 threads per SM.
+__global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
     extern __shared__ double q_mem[];   // blockDim.x * kPropQueueBytesPerThread bytes
     const int QB = 2 * blockDim.x;
     double* q_d = q_mem;
@@ -662,7 +670,7 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
     // warp overshoots the room by at most one round of its own writes
     int seen_child = *(volatile int*)&cnt->n_child;
     // statistics, kept per thread and added to the counters once when the block ends
-    unsigned n_prop = 0, n_chain = 0, n_exam = 0, n_occ = 0, n_comp = 0;
+    unsigned n_prop = 0, n_chain = 0, n_exam = 0, n_occ = 0, n_comp = 0, n_ray = 0;
     if (t == 0) {
         for (int i = 0; i < 3; ++i) s_nq[i] = s_dry[i] = 0;
     }
@@ -672,12 +680,12 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
         const int nq = min(s_nq[r % 3], (int)blockDim.x);
         const bool dry = s_dry[r % 3] != 0;
         if (nq == 0 && dry) {                      // uniform over the block
-            const unsigned sums[5] = {__reduce_add_sync(full, n_prop), __reduce_add_sync(full, n_chain),
+            const unsigned sums[6] = {__reduce_add_sync(full, n_prop), __reduce_add_sync(full, n_chain),
                                       __reduce_add_sync(full, n_exam), __reduce_add_sync(full, n_occ),
-                                      __reduce_add_sync(full, n_comp)};
-            unsigned long long* dst[5] = {&cnt->propagated, &cnt->chained, &cnt->examined, &cnt->occupied,
-                                          &cnt->children};
-            if (lane < 5 && sums[lane]) atomicAdd(dst[lane], (unsigned long long)sums[lane]);
+                                      __reduce_add_sync(full, n_comp), __reduce_add_sync(full, n_ray)};
+            unsigned long long* dst[6] = {&cnt->propagated, &cnt->chained, &cnt->examined, &cnt->occupied,
+                                          &cnt->children, &cnt->rays};
+            if (lane < 6 && sums[lane]) atomicAdd(dst[lane], (unsigned long long)sums[lane]);
             break;
         }
         if (t == 0) {
@@ -713,14 +721,14 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
         }
         if (!__any_sync(full, have)) continue;     // this warp idles this round
         ChildOut c0, c1;
-        int nch = 0, occ = 0, ncomp = 0;
+        int nch = 0, occ = 0, ncomp = 0, nray = 0;
         bool prop = false;
         const int wo = wb * blockDim.x;
         const TaskQueue tq{q_d + wo, q_A + wo, q_B + wo, q_px + wo, q_py + wo, q_IA + wo, q_IB + wo,
                            q_he + wo, q_inst + wo, q_src + wo, q_hop + wo, &s_nq[(r + 1) % 3], (int)blockDim.x};
         if (have)
             prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, task, hop, tq, c0, c1, nch, occ,
-                                    ncomp, cIA, cIB);
+                                    ncomp, nray, cIA, cIB);
         bool cont = have && nch > 0 && hop + 1 < hops && le_s(c0.key, w.ctl[inst].tau) &&
                     (!dry || nq >= tail_cut) && seen_child < room;
         // the continuing child goes to the queue while it has room, every other child to
@@ -752,6 +760,7 @@ __global__ void __launch_bounds__(kPropMaxBlock, 2) k_propagate(Work w, int hops
         n_exam += have && !task ? 1u : 0u;
         n_occ += (unsigned)occ;
         n_comp += (unsigned)ncomp;
+        n_ray += (unsigned)nray;
     }
 }
 
@@ -1401,11 +1410,15 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         stats->windows_occupied = (int64_t)c.occupied;
         stats->children_computed = (int64_t)c.children;
         // algorithmic FP64 operations of k_propagate (add, sub, mul, div, sqrt = 1; fma = 2),
-        // counted per code path of propagate_window: filter 17 (11 for a chained window,
-        // whose |IA|, |IB| come from its parent), passed window +11, occupied v2 +20,
-        // each child computed +50 (30.5 plus 13 per ray intersected)
-        stats->prop_fp64_ops = (int64_t)(17ull * c.examined + 11ull * c.propagated + 20ull * c.occupied +
-                                         50ull * c.children) - (int64_t)(6ull * c.chained);
+        // counted per code path of propagate_window: a window taken from the work list 7
+        // (2 offsets, 5 for the endpoint filter), a chained window 2 (its filter was its
+        // parent's child filter), a window that passed +10 (snap tolerance and occupancy
+        // test), an occupied one +14 (crossing point, |I v2|, event distance), a child
+        // +32 (frame change 13, width test 2, child filter 16, key 1) plus 8 per ray
+        // intersected (two per child, one when the window occupies v2)
+        const unsigned long long fresh = c.examined > c.chained ? c.examined - c.chained : 0ull;
+        stats->prop_fp64_ops = (int64_t)(7ull * fresh + 2ull * c.chained + 10ull * c.propagated +
+                                         14ull * c.occupied + 32ull * c.children + 8ull * c.rays);
         for (int p = 0; p < 6; ++p) stats->ms_phase[p] = phase_ms[p];
     }
     return PCH_OK;
