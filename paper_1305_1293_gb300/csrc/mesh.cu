@@ -171,11 +171,12 @@ __global__ void k_twins(int nh, const int* __restrict__ tri, const unsigned long
 // counter-clockwise), record the ring order, angular positions and total angle.
 __global__ void k_rings(int nv, const int* __restrict__ twin, const int* __restrict__ vout,
                         const int* __restrict__ vstart, const double* __restrict__ hang, int* vlist,
-                        double* vphi, double* vtheta, unsigned char* vflag, int* err) {
+                        float* vphi, float* vtheta, float* hang_f, double2* vrot, double2* vtrot,
+                        unsigned char* vflag, int* err) {
     const double kTwoPi = 6.283185307179586476925286766559;
     for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x) {
         int cnt = vstart[v + 1] - vstart[v];
-        if (cnt == 0) { vtheta[v] = 0; vflag[v] = 0; continue; }
+        if (cnt == 0) { vtheta[v] = 0; vtrot[v] = make_double2(1.0, 0.0); vflag[v] = 0; continue; }
         int h0 = vout[v];
         int start = h0;
         bool boundary = false;
@@ -191,7 +192,11 @@ __global__ void k_rings(int nv, const int* __restrict__ twin, const int* __restr
         double phi = 0.0;
         while (k < cnt) {
             vlist[vstart[v] + k] = h;
-            vphi[h] = phi;
+            vphi[h] = (float)phi;
+            hang_f[h] = (float)hang[h];
+            double sp, cp;
+            sincos(phi, &sp, &cp);
+            vrot[h] = make_double2(cp, sp);
             phi += hang[h];
             ++k;
             int t = twin[he_prev(h)];           // counter-clockwise: h -> twin(prev(h))
@@ -199,7 +204,12 @@ __global__ void k_rings(int nv, const int* __restrict__ twin, const int* __restr
             h = t;
         }
         if (k != cnt) atomicOr(err, kMeshErrFan);
-        vtheta[v] = phi;
+        vtheta[v] = (float)phi;
+        {
+            double sp, cp;
+            sincos(phi, &sp, &cp);
+            vtrot[v] = make_double2(cp, sp);
+        }
         unsigned char f = boundary ? 1 : 0;
         // Saddle (total angle above 2 pi, Section 3) or boundary vertex: a pseudo-source
         // candidate.  The 1e-9 band keeps flat vertices in the candidate set (superset).
@@ -267,7 +277,7 @@ __global__ void __launch_bounds__(256) k_stats_final(const double* part_l, const
 
 static void free_mesh(DevMesh& d) {
     cudaFree(d.rec); cudaFree(d.vstart); cudaFree(d.vlist); cudaFree(d.hang);
-    cudaFree(d.vtheta); cudaFree(d.vphi); cudaFree(d.vflag);
+    cudaFree(d.vtheta); cudaFree(d.vphi); cudaFree(d.vflag); cudaFree(d.vrot); cudaFree(d.vtrot);
     d = DevMesh{};
 }
 
@@ -299,6 +309,7 @@ extern "C" pch_status pch_create_mesh(const double* vertices, int32_t n_vertices
         *hvals = nullptr, *counts = nullptr;
     unsigned long long* hkeys = nullptr;
     double* lsum = nullptr;
+    double* hang64 = nullptr;
     unsigned long long cap = 1;
     while (cap < 2ull * (unsigned long long)nh) cap <<= 1;
     pch_status st = PCH_OK;
@@ -319,11 +330,14 @@ extern "C" pch_status pch_create_mesh(const double* vertices, int32_t n_vertices
         MCHK(cudaMalloc(&xyz, sizeof(double) * 3 * nv));
         MCHK(cudaMalloc(&tri, sizeof(int) * nh));
         MCHK(cudaMalloc(&d.rec, sizeof(HERec) * nh));
-        MCHK(cudaMalloc(&d.hang, sizeof(double) * nh));
-        MCHK(cudaMalloc(&d.vphi, sizeof(double) * nh));
+        MCHK(cudaMalloc(&hang64, sizeof(double) * nh));
+        MCHK(cudaMalloc(&d.hang, sizeof(float) * nh));
+        MCHK(cudaMalloc(&d.vphi, sizeof(float) * nh));
         MCHK(cudaMalloc(&d.vlist, sizeof(int) * nh));
         MCHK(cudaMalloc(&d.vstart, sizeof(int) * (nv + 1)));
-        MCHK(cudaMalloc(&d.vtheta, sizeof(double) * nv));
+        MCHK(cudaMalloc(&d.vtheta, sizeof(float) * nv));
+        MCHK(cudaMalloc(&d.vrot, sizeof(double2) * nh));
+        MCHK(cudaMalloc(&d.vtrot, sizeof(double2) * nv));
         MCHK(cudaMalloc(&d.vflag, nv));
         MCHK(cudaMalloc(&twin, sizeof(int) * nh));
         MCHK(cudaMalloc(&vcount, sizeof(int) * (nv + 1)));
@@ -343,12 +357,13 @@ extern "C" pch_status pch_create_mesh(const double* vertices, int32_t n_vertices
         const int tb = 256;
         const int gb = std::max(1, std::min((nh + tb - 1) / tb, sm_count() * 8));
         const int gv = std::max(1, std::min((nv + tb - 1) / tb, sm_count() * 8));
-        k_frames<<<gb, tb>>>(nh, xyz, tri, d.rec, d.hang, err);
+        k_frames<<<gb, tb>>>(nh, xyz, tri, d.rec, hang64, err);
         k_hash_insert<<<gb, tb>>>(nh, tri, hkeys, hvals, cap - 1, err);
         k_twins<<<gb, tb>>>(nh, tri, hkeys, hvals, cap - 1, twin, vcount, vout);
         MCHK(cudaGetLastError());
         MCHK(exclusive_scan(vcount, d.vstart, nv + 1, scan_tmp, 0));
-        k_rings<<<gv, tb>>>(nv, twin, vout, d.vstart, d.hang, d.vlist, d.vphi, d.vtheta, d.vflag, err);
+        k_rings<<<gv, tb>>>(nv, twin, vout, d.vstart, hang64, d.vlist, d.vphi, d.vtheta, d.hang, d.vrot, d.vtrot,
+                            d.vflag, err);
         k_rec_ids<<<gb, tb>>>(nh, twin, d.vflag, d.rec);
         k_stats<<<kStatBlocks, 256>>>(nh, nv, d.rec, twin, d.vflag, lsum + 1, counts + 2);
         k_stats_final<<<1, kStatBlocks>>>(lsum + 1, counts + 2, lsum, counts);
@@ -372,7 +387,7 @@ extern "C" pch_status pch_create_mesh(const double* vertices, int32_t n_vertices
 cleanup:
 #undef MCHK
     cudaFree(xyz); cudaFree(tri); cudaFree(twin); cudaFree(vcount); cudaFree(vout); cudaFree(err);
-    cudaFree(scan_tmp); cudaFree(hkeys); cudaFree(hvals); cudaFree(counts); cudaFree(lsum);
+    cudaFree(scan_tmp); cudaFree(hkeys); cudaFree(hvals); cudaFree(counts); cudaFree(lsum); cudaFree(hang64);
     if (st != PCH_OK) free_mesh(d);
     return st;
 }

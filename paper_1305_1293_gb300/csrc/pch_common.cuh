@@ -51,9 +51,13 @@ struct DevMesh {
     HERec* rec;            // [nh]
     int* vstart;           // [nv + 1] CSR of outgoing half-edges, one-ring order
     int* vlist;            // [nh]
-    double* hang;          // [nh] corner angle at the start vertex of each half-edge
-    double* vtheta;        // [nv] total angle (Section 3)
-    double* vphi;          // [nh] angular position of each outgoing half-edge around its start vertex
+    // angles, kept in FP32: they only steer the pseudo-source fans, whose wedges are
+    // widened far beyond FP32 rounding (the saddle test itself is made in FP64)
+    float* hang;           // [nh] corner angle at the start vertex of each half-edge
+    float* vtheta;         // [nv] total angle (Section 3)
+    float* vphi;           // [nh] angular position of each outgoing half-edge around its start vertex
+    double2* vrot;         // [nh] (cos, sin) of vphi, FP64: exact directions without trigonometry
+    double2* vtrot;        // [nv] (cos, sin) of vtheta
     unsigned char* vflag;  // [nv] bit0 boundary, bit1 pseudo-source capable
 };
 
@@ -78,9 +82,11 @@ struct Inst {
     const HERec* rec;
     const int* vstart;
     const int* vlist;
-    const double* vphi;         // angular position of every half-edge around its start vertex
-    const double* vtheta;       // total angle per vertex
-    const double* hang;         // corner angle at the start vertex of every half-edge
+    const float* vphi;          // angular position of every half-edge around its start vertex
+    const float* vtheta;        // total angle per vertex
+    const float* hang;          // corner angle at the start vertex of every half-edge
+    const double2* vrot;        // (cos, sin) of the angular position of every half-edge
+    const double2* vtrot;       // (cos, sin) of the total angle of every vertex
     const unsigned char* vflag; // bit0: boundary vertex
     unsigned long long* g;      // geod_dist[] as ordered u64 images of nonnegative doubles
     unsigned long long* ang;    // angle_split[]: packed (rounded-up distance, crossing position)
@@ -136,15 +142,24 @@ enum : int {
     kErrNaN = 8,
 };
 
+// A pseudo-source fan candidate: a distance event at a saddle or boundary vertex, with
+// the direction it arrived from.
+struct FanReq {
+    int inst;
+    unsigned v;
+    int href;       // half-edge leaving v whose frame holds (dx, dy); -1: every direction
+    int pad;
+    double D;       // the event's distance
+    double dx, dy;  // from v towards the event's pseudo-source, in href's frame
+};
+
 // Capacities and buffers of the solve workspace.
 struct Work {
     WinSoA pool[2];         // current / next pending pool
     WinSoA sel;             // selected windows
     WinSoA arena;           // children of this iteration (unsorted)
     int pool_cap, sel_cap, arena_cap, req_cap;
-    int2* req[2];           // fan candidates (inst, vertex)
-    double4* req_d[2];      // fan candidates: distance, reference angle, incoming direction (dx, dy)
-                            // in the reference half-edge's frame (NaN = all directions)
+    FanReq* req[2];         // fan candidates of this and of the next iteration
     unsigned* sort_key[2];
     int* sort_val[2];
     int* sort_hist;         // radix histograms

@@ -97,27 +97,18 @@ __device__ __forceinline__ bool vertex_event(const Inst& I, unsigned vf, double 
     return false;
 }
 
-// A fan candidate carries the incoming ray as a direction (dx, dy) in the frame of a
-// reference half-edge leaving v whose angular position is `base`; the fan kernel turns
-// it into an angle (atan2) only for candidates that still hold the vertex's distance.
-__device__ __forceinline__ void push_fan(int2* req, double4* req_d, int* n, int cap, int* err, int inst, unsigned v,
-                                         double D, double base, double dx, double dy) {
+// A fan candidate carries the incoming ray as a direction (dx, dy), of any length, in
+// the frame of a reference half-edge href leaving v (href < 0: every direction).
+__device__ __forceinline__ void push_fan(FanReq* req, int* n, int cap, int* err, int inst, unsigned v, double D,
+                                         int href, double dx, double dy) {
     int slot = atomicAdd(n, 1);
     if (slot < cap) {
-        req[slot] = make_int2(inst, (int)v);
-        req_d[slot] = make_double4(D, base, dx, dy);
+        FanReq r;
+        r.inst = inst; r.v = v; r.href = href; r.pad = 0; r.D = D; r.dx = dx; r.dy = dy;
+        req[slot] = r;
     } else {
         atomicOr(err, kErrReqFull);
     }
-}
-
-// Angular coordinate of a direction at vertex v: interior vertices wrap modulo the total
-// angle, boundary vertices clamp to [0, total angle].
-__device__ __forceinline__ double wrap_angle(const Inst& I, unsigned v, double a) {
-    double T = I.vtheta[v];
-    if (I.vflag[v] & 1) return fmin(fmax(a, 0.0), T);
-    a = fmod(a, T);
-    return a < 0.0 ? a + T : a;
 }
 
 __device__ __forceinline__ int hist_bin(double key, double ref, double ilbar) {
@@ -208,8 +199,7 @@ __global__ void k_init_sources(Work w, const SrcDev* __restrict__ srcs, int n_sr
         if (s.kind == 0) {
             I.g[s.vertex] = 0ull;
             // the source's fan covers every direction
-            push_fan(w.req[0], w.req_d[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, (unsigned)s.vertex, 0.0, 0.0,
-                     NAN, NAN);
+            push_fan(w.req[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, (unsigned)s.vertex, 0.0, -1, 0.0, 0.0);
         }
     }
 }
@@ -232,8 +222,7 @@ __global__ void k_init_face_sources(Work w, const SrcDev* __restrict__ srcs, int
             double gc = ldg_dist(I.g, R.v0 & ~kPseudoBit);
             if (vertex_event(I, R.v0, dstart, gc)) {
                 // incoming direction: from the corner towards the point, inside face(h)
-                push_fan(w.req[0], w.req_d[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, R.v0 & ~kPseudoBit,
-                         dstart, I.vphi[h], x, y);
+                push_fan(w.req[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, R.v0 & ~kPseudoBit, dstart, h, x, y);
             }
             if (R.twin < 0) continue;
             // window on twin(h) = (v1 -> v0): point at (L - x, -y), interval [0, L]
@@ -454,7 +443,7 @@ constexpr int kHopTask = 1 << 30;   // hop-field flag of a queue entry: a deferr
 // both children exist the left one is deferred to q as a task (if q has room).  A task
 // (task = true) skips the window's own part, done in an earlier round, and computes the
 // left child only; IB_in then holds |I v2|.
-__device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, int2* req, double4* req_d, int inst,
+__device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, FanReq* req, int inst,
                                                  int src, double d, int h, double A, double B, double px, double py,
                                                  bool task, int hop, const TaskQueue& q, ChildOut& c0, ChildOut& c1,
                                                  int& nch, int& occ_out, int& ncomp, int& nray, double IA_in,
@@ -496,15 +485,13 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
             if (le_s(A, tol)) {
                 double D0 = d + (sbits(A) == 0 ? IA : sqrt(px * px + py2));
                 if (vertex_event(I, R.v0, D0, g0))   // the ray arrives at v0 from I (h's frame)
-                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v0 & ~kPseudoBit, D0,
-                             I.vphi[h], px, py);
+                    push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v0 & ~kPseudoBit, D0, h, px, py);
             }
             if (le_s(L - tol, B)) {
                 double q = L - px;
                 double D1 = d + (sbits(B) == sbits(L) ? IB : sqrt(q * q + py2));
                 if (vertex_event(I, R.v1, D1, g1))   // at v1, in the frame of twin(h) = (v1 -> v0)
-                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v1 & ~kPseudoBit, D1,
-                             I.vphi[R.twin], q, -py);
+                    push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v1 & ~kPseudoBit, D1, R.twin, q, -py);
             }
             // occupancy of v2: the ray I -> v2 crosses e at xs = px + num / den;
             // decided without the division (den > 0), by the signs of fused residuals
@@ -540,8 +527,8 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, i
                     // prev(h) = (v2 -> v0), whose axis is (-xc, -yc) / L2
                     const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
                     const double ux = -xc * R.iL2, uy = -yc * R.iL2, ex = px - xc, ey = py - yc;
-                    push_fan(req, req_d, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v2 & ~kPseudoBit, D2,
-                             I.vphi[hp], ex * ux + ey * uy, ux * ey - uy * ex);
+                    push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v2 & ~kPseudoBit, D2, hp,
+                             ex * ux + ey * uy, ux * ey - uy * ex);
                 }
                 if (le_s(B - xcl, tiny)) right = false;
                 if (le_s(xcl - A, tiny)) left = false;
@@ -663,8 +650,7 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
     const unsigned lt = (1u << lane) - 1u;
     const int it = cnt->iter;
     const int n = min(cnt->n_sel, w.sel_cap);
-    int2* req = w.req[it & 1];
-    double4* req_d = w.req_d[it & 1];
+    FanReq* req = w.req[it & 1];
     const int room = w.arena_cap / 2 - 2 * (int)(gridDim.x * blockDim.x);
     // the arena fill this warp last saw (updated whenever it reserves arena slots): a
     // warp overshoots the room by at most one round of its own writes
@@ -727,7 +713,7 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
         const TaskQueue tq{q_d + wo, q_A + wo, q_B + wo, q_px + wo, q_py + wo, q_IA + wo, q_IB + wo,
                            q_he + wo, q_inst + wo, q_src + wo, q_hop + wo, &s_nq[(r + 1) % 3], (int)blockDim.x};
         if (have)
-            prop = propagate_window(w, cnt, req, req_d, inst, src, d, h, A, B, px, py, task, hop, tq, c0, c1, nch, occ,
+            prop = propagate_window(w, cnt, req, inst, src, d, h, A, B, px, py, task, hop, tq, c0, c1, nch, occ,
                                     ncomp, nray, cIA, cIB);
         bool cont = have && nch > 0 && hop + 1 < hops && le_s(c0.key, w.ctl[inst].tau) &&
                     (!dry || nq >= tail_cut) && seen_child < room;
@@ -770,161 +756,195 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
 // the directions at least pi away from the incoming ray on both sides (a wedge of width
 // total angle - 2 pi at an interior saddle; at a boundary vertex the directions that
 // wrap around it).  Boundary edges get their endpoint events instead of a window.
-constexpr double kPi = 3.14159265358979323846;
-constexpr double kWedgeEps = 1e-9;    // the wedge is widened by this angle on each side
+//
+// No trigonometry at fan time: the mesh keeps, for every half-edge leaving a vertex, the
+// unit complex number of its angular position, and for every vertex that of its total
+// angle.  The incoming direction times its reference half-edge's number is the incoming
+// ray in the vertex's angular frame; the wedge boundaries are that ray turned by pi (and
+// by the total angle), and turned back into a corner's own frame by the conjugate of the
+// corner's number: a few FP64 products, then one division for the point on the opposite
+// edge.  FP32 angles (good to about 1e-6 radians) only pick the corners a boundary may
+// fall in, with a margin; a boundary that proves to lie outside its corner clamps to the
+// corner's end, so the choice never changes a window.
+constexpr float kPiF = 3.14159265358979f;
+constexpr float kFanPickMargin = 1e-4f;   // radians: corners within this of a wedge boundary are computed exactly
+constexpr double kFanWiden = 1e-9;        // interval widening for FP64 rounding, relative to the edge length
+constexpr int kFanLanes = 8;              // lanes per fan candidate (corners handled in turn)
 
-struct Wedges {
-    double lo[2], hi[2];
-    int n;
-    int shifts;     // interior vertices: test the wedge shifted by -T, 0, +T
-};
-
-__device__ __forceinline__ Wedges make_wedges(bool boundary, double T, double phi, bool full) {
-    Wedges W;
-    W.n = 0;
-    W.shifts = 0;
-    if (full || !(phi == phi)) {
-        W.lo[0] = -1e300; W.hi[0] = 1e300; W.n = 1;
-        return W;
-    }
-    if (boundary) {
-        if (phi - kPi > -kWedgeEps) { W.lo[W.n] = -1.0; W.hi[W.n] = phi - kPi + kWedgeEps; ++W.n; }
-        if (phi + kPi < T + kWedgeEps) { W.lo[W.n] = phi + kPi - kWedgeEps; W.hi[W.n] = T + 1.0; ++W.n; }
-    } else if (T - 2.0 * kPi > -kWedgeEps) {
-        W.lo[0] = phi + kPi - kWedgeEps; W.hi[0] = phi + T - kPi + kWedgeEps; W.n = 1; W.shifts = 1;
-    }
-    return W;
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) {   // a * conj(b)
+    return make_double2(fma(a.x, b.x, a.y * b.y), fma(a.y, b.x, -a.x * b.y));
 }
 
-// Part [b0, b1] (angles from the face's first edge at the vertex) of corner [c0, c0 + c]
-// covered by the wedges; false if none.
-__device__ __forceinline__ bool wedge_part(const Wedges& W, double T, double c0, double c, double& b0, double& b1) {
-    for (int wi = 0; wi < W.n; ++wi)
-        for (int j = -W.shifts; j <= W.shifts; ++j) {
-            double a = fmax(W.lo[wi] + j * T, c0), b = fmin(W.hi[wi] + j * T, c0 + c);
-            if (b >= a) {
-                b0 = a - c0;
-                b1 = b - c0;
-                return true;
-            }
-        }
-    return false;
+// Where the ray from the apex v of o's face along z (relative to the direction
+// v -> start(o), any length) meets o: distance from start(o), clamped to [0, L].
+__device__ __forceinline__ double fan_hit(const HERec& Ro, double2 z) {
+    const double ux = -Ro.xc * Ro.iL2, uy = -Ro.yc * Ro.iL2;   // v -> start(o), unit
+    const double dx = fma(ux, z.x, -uy * z.y), dy = fma(ux, z.y, uy * z.x);
+    if (!(dy < 0.0)) return dx > 0.0 ? Ro.L : 0.0;             // parallel to o or turned away
+    const double s = fma(-Ro.yc * dx, rcp_nr(dy), Ro.xc);
+    return s < 0.0 ? 0.0 : (s > Ro.L ? Ro.L : s);
 }
 
-// Where the ray from the apex v of o's face, at angle beta from v->start(o), meets o:
-// distance from start(o) along o (o's frame: start at 0, v at (xc, yc)).
-__device__ __forceinline__ double fan_hit(const HERec& Ro, double beta) {
-    double sb, cb;
-    sincos(beta, &sb, &cb);
-    const double iva = 1.0 / Ro.L2;
-    const double ux = -Ro.xc * iva, uy = -Ro.yc * iva;
-    const double dx = ux * cb - uy * sb, dy = ux * sb + uy * cb;
-    double s = Ro.xc - Ro.yc * dx / dy;
-    return fmin(fmax(s, 0.0), Ro.L);
-}
-
-// One warp per fan candidate; lane j handles face j of the vertex's one-ring.
+// kFanLanes lanes per fan candidate; lane j of the group handles corners j, j + 8, ...
+// of the vertex's one-ring.
 __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
     Counters* cnt = w.cnt;
     if (cnt->halt) return;
-    const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
-    const unsigned lt = (1u << lane) - 1u;
+    const int sl = lane & (kFanLanes - 1);
+    const int lead = lane & ~(kFanLanes - 1);
+    const unsigned gmask = ((1u << kFanLanes) - 1u) << lead;
+    const unsigned below = (1u << sl) - 1u;
     const int it = cnt->iter;
     const int nreq = min(cnt->n_req, w.req_cap);
     if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&cnt->fan_cand, (unsigned long long)nreq);
-    const int2* req = w.req[it & 1];
-    const double4* req_d = w.req_d[it & 1];
-    int2* req_nx = w.req[(it + 1) & 1];
-    double4* req_d_nx = w.req_d[(it + 1) & 1];
+    const FanReq* req = w.req[it & 1];
+    FanReq* req_nx = w.req[(it + 1) & 1];
     const unsigned stamp_fan = (unsigned)it + 1u;
-    const int warp0 = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nwarps = (gridDim.x * blockDim.x) >> 5;
-    for (int r = warp0; r < nreq; r += nwarps) {
-        const int inst = req[r].x;
-        const unsigned v = (unsigned)req[r].y;
-        const double4 rq = req_d[r];
-        const double D = rq.x;
-        const Inst& I = w.inst[inst];
+    const int group0 = (blockIdx.x * blockDim.x + threadIdx.x) / kFanLanes;
+    const int ngroups = (gridDim.x * blockDim.x) / kFanLanes;
+    unsigned n_fans = 0, n_fwin = 0;
+    for (int r = group0; r < nreq; r += ngroups) {     // uniform over the group
+        const FanReq rq = req[r];
+        const unsigned v = rq.v;
+        const double D = rq.D;
+        const Inst& I = w.inst[rq.inst];
         int ok = 0;
-        if (lane == 0) {
+        if (sl == 0) {
             // still the vertex's distance (not superseded), and the first fan this iteration
             ok = dbits(D) == __ldcg(I.g + v) && atomicExch(I.stamp + v, stamp_fan) != stamp_fan;
-            if (ok) atomicAdd(&cnt->fans, 1ull);
+            n_fans += ok ? 1u : 0u;
         }
-        if (!__shfl_sync(full, ok, 0)) continue;
+        if (!__shfl_sync(gmask, ok, lead)) continue;
         const int s = I.vstart[v], e = I.vstart[v + 1];
-        const double T = I.vtheta[v];
-        // incoming direction as an angle around v (NaN: the source, every direction)
-        const double phi = rq.z == rq.z ? wrap_angle(I, v, rq.y + atan2(rq.w, rq.z)) : rq.z;
-        const Wedges W = make_wedges(I.vflag[v] & 1, T, phi, full_fan != 0);
-        if (W.n == 0) continue;
+        const bool boundary = (I.vflag[v] & 1) != 0;
+        const bool all = full_fan != 0 || rq.href < 0;
+        // wedges in FP32 angular coordinates, unwrapped (interior ones are tested at
+        // shifts of the total angle T): interior [phi + pi, phi + T - pi]; boundary
+        // [-inf, phi - pi] and [phi + pi, +inf]
+        const float T = I.vtheta[v];
+        double2 za = make_double2(0.0, 0.0), zb = za, tr = make_double2(1.0, 0.0);
+        int nw = 0;
+        float wlo[2] = {0.f, 0.f}, whi[2] = {0.f, 0.f};
+        bool lo_open[2] = {false, false}, hi_open[2] = {false, false};
+        if (!all) {
+            float phi = I.vphi[rq.href] + atan2f((float)rq.dy, (float)rq.dx);
+            // the incoming ray in the vertex's angular frame, turned by pi: the direction of
+            // phi + pi (and of phi - pi); zb is that of phi + T - pi
+            const double2 E = cmul(I.vrot[rq.href], make_double2(rq.dx, rq.dy));
+            za = make_double2(-E.x, -E.y);
+            tr = I.vtrot[v];
+            zb = cmul(za, tr);
+            if (boundary) {
+                phi = fminf(fmaxf(phi, 0.f), T);
+                if (phi - kPiF > -kFanPickMargin) {
+                    wlo[nw] = -1e30f; whi[nw] = phi - kPiF; lo_open[nw] = true; ++nw;
+                }
+                if (phi + kPiF < T + kFanPickMargin) {
+                    wlo[nw] = phi + kPiF; whi[nw] = 1e30f; hi_open[nw] = true; ++nw;
+                }
+            } else if (T - 2.f * kPiF > -kFanPickMargin) {
+                wlo[0] = phi + kPiF; whi[0] = phi + T - kPiF; nw = 1;
+            }
+            if (nw == 0) continue;
+        }
         bool deferred = false;
-        for (int j0 = s; j0 < e && !deferred; j0 += 32) {
-            const int j = j0 + lane;
-            double b0 = 0.0, b1 = 0.0, c = 0.0;
+        for (int j0 = s; j0 < e && !deferred; j0 += kFanLanes) {
+            const int j = j0 + sl;
             bool has = false;
             int o = 0;
+            double s0 = 0.0, s1 = 0.0;
             HERec Ro;
             if (j < e) {
                 const int hv = I.vlist[j];
-                c = I.hang[hv];
-                has = wedge_part(W, T, I.vphi[hv], c, b0, b1);
+                bool ex0 = false, ex1 = false, zend_b = false;
+                int shift = 0;
+                if (all) {
+                    has = true;
+                } else {
+                    const float c0 = I.vphi[hv], c1 = c0 + I.hang[hv];
+                    for (int k = 0; k < nw && !has; ++k)
+                        for (int sh = boundary ? 0 : -2; sh <= (boundary ? 0 : 1) && !has; ++sh) {
+                            const float lo = wlo[k] + (float)sh * T, hi = whi[k] + (float)sh * T;
+                            if (hi >= c0 - kFanPickMargin && lo <= c1 + kFanPickMargin) {
+                                // a corner (under pi) meets at most one wedge at one shift
+                                has = true;
+                                shift = sh;
+                                ex0 = !lo_open[k] && lo > c0 - kFanPickMargin;
+                                ex1 = !hi_open[k] && hi < c1 + kFanPickMargin;
+                                zend_b = !boundary;
+                            }
+                        }
+                }
                 if (has) {
                     o = he_next(hv);                   // edge (a -> b) opposite v
                     Ro = I.rec[o];
+                    s0 = 0.0;
+                    s1 = Ro.L;
+                    if (ex0 || ex1) {
+                        // boundary directions in the corner's frame: z e^(i shift T) conj(rot(hv))
+                        double2 t = make_double2(1.0, 0.0);
+                        if (shift == 1) t = tr;
+                        else if (shift == -1) t = make_double2(tr.x, -tr.y);
+                        else if (shift == -2) t = cmul_conj(make_double2(tr.x, -tr.y), tr);
+                        const double2 cr = I.vrot[hv];
+                        if (ex0) s0 = fmax(fan_hit(Ro, cmul_conj(cmul(za, t), cr)) - kFanWiden * Ro.L, 0.0);
+                        if (ex1) s1 = fmin(fan_hit(Ro, cmul_conj(cmul(zend_b ? zb : za, t), cr)) + kFanWiden * Ro.L, Ro.L);
+                    }
                 }
             }
             const bool win = has && Ro.twin >= 0;
-            const unsigned bal = __ballot_sync(full, win);
+            const unsigned bal = (__ballot_sync(gmask, win) >> lead) & ((1u << kFanLanes) - 1u);
             const int cntw = __popc(bal);
             int base = 0;
-            if (lane == 0 && cntw) base = atomicAdd(&cnt->n_child, cntw);
-            base = __shfl_sync(full, base, 0);
+            if (sl == 0 && cntw) base = atomicAdd(&cnt->n_child, cntw);
+            base = __shfl_sync(gmask, base, lead);
             if (base + cntw > w.arena_cap) {
                 // no room this iteration: mark the reserved slots empty, retry next iteration
-                const int sl = base + __popc(bal & lt);
-                if (win && sl < w.arena_cap) w.arena.he[sl] = -1;
-                if (lane == 0) {
+                const int sl2 = base + __popc(bal & below);
+                if (win && sl2 < w.arena_cap) w.arena.he[sl2] = -1;
+                if (sl == 0) {
                     atomicExch(I.stamp + v, 0u);
-                    push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, v, D, rq.y, rq.z, rq.w);
+                    push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, v, D, rq.href, rq.dx, rq.dy);
                 }
                 deferred = true;
                 continue;
             }
             if (!has) continue;
             const double Lo = Ro.L;
-            const double s0 = b0 <= 1e-12 ? 0.0 : fan_hit(Ro, b0);
-            const double s1 = b1 >= c - 1e-12 ? Lo : fan_hit(Ro, b1);
             if (!win) {
                 // boundary edge: endpoint events for the covered endpoints
                 const unsigned a = Ro.v0 & ~kPseudoBit, b = Ro.v1 & ~kPseudoBit;
                 double ga = ldg_dist(I.g, a), gb = ldg_dist(I.g, b);
-                // incoming directions: at a towards v is the far side of o's corner; at b it
-                // is the direction of next(o) = (b -> v)
+                // incoming directions: at a towards v, in o's frame; at b along next(o) = (b -> v)
                 if (s0 <= 0.0 && vertex_event(I, Ro.v0, D + Ro.L2, ga))
-                    push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, a, D + Ro.L2,
-                             I.vphi[o], Ro.xc, Ro.yc);
+                    push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, a, D + Ro.L2, o, Ro.xc, Ro.yc);
                 if (s1 >= Lo && vertex_event(I, Ro.v1, D + Ro.L1, gb))
-                    push_fan(req_nx, req_d_nx, &cnt->n_req_next, w.req_cap, &cnt->error, inst, b, D + Ro.L1,
-                             I.vphi[he_next(o)], 1.0, 0.0);
+                    push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, b, D + Ro.L1, he_next(o), 1.0,
+                             0.0);
                 continue;
             }
             // window on twin(o) = (b -> a): I = v at (Lo - xc, -yc), interval [Lo - s1, Lo - s0]
-            const int sl = base + __popc(bal & lt);
+            const int slot = base + __popc(bal & below);
             const double A = Lo - s1, B = Lo - s0;
             const double px = Lo - Ro.xc, py = -Ro.yc;
-            const double IA = sqrt((A - px) * (A - px) + py * py), IB = sqrt((B - px) * (B - px) + py * py);
+            const double IA = sqrt_nr(fma(A - px, A - px, py * py)), IB = sqrt_nr(fma(B - px, B - px, py * py));
             const double ga = ldg_dist(I.g, Ro.v0 & ~kPseudoBit), gb = ldg_dist(I.g, Ro.v1 & ~kPseudoBit);
             if (!(B - A > kEpsTiny * Lo) || dominated(D + IB, gb + B) || dominated(D + IA, ga + (Lo - A))) {
-                w.arena.he[sl] = -1;
+                w.arena.he[slot] = -1;
                 continue;
             }
             const double key = D + (px < A ? IA : (px > B ? IB : -py));
-            store_win(w.arena, sl, Ro.twin, inst, D, A, B, px, py, key, (int)v, IA, IB);
-            atomicAdd(&cnt->fan_windows, 1ull);
+            store_win(w.arena, slot, Ro.twin, rq.inst, D, A, B, px, py, key, (int)v, IA, IB);
+            ++n_fwin;
         }
     }
+    const unsigned f1 = __reduce_add_sync(0xffffffffu, n_fans), f2 = __reduce_add_sync(0xffffffffu, n_fwin);
+    if (lane == 0 && f1) atomicAdd(&cnt->fans, (unsigned long long)f1);
+    if (lane == 0 && f2) atomicAdd(&cnt->fan_windows, (unsigned long long)f2);
 }
 
 // ====================================================================== Step 3/4: append
@@ -1139,8 +1159,6 @@ static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap, int req
     if (!e) e = alloc_soa(fresh, nw.arena, arena_cap);
     if (!e) e = fresh.get(&nw.req[0], req_cap);
     if (!e) e = fresh.get(&nw.req[1], req_cap);
-    if (!e) e = fresh.get(&nw.req_d[0], req_cap);
-    if (!e) e = fresh.get(&nw.req_d[1], req_cap);
     if (!e) e = fresh.get(&nw.sort_key[0], arena_cap);
     if (!e) e = fresh.get(&nw.sort_key[1], arena_cap);
     if (!e) e = fresh.get(&nw.sort_val[0], arena_cap);
@@ -1166,8 +1184,7 @@ static pch_status ensure_pools(Workspace* ws, int sel_cap, int pool_cap, int req
             cudaMemcpy(nw.pool[p].src, w.pool[p].src, n * 4, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.pool[p].IA, w.pool[p].IA, n * 8, cudaMemcpyDeviceToDevice);
             cudaMemcpy(nw.pool[p].IB, w.pool[p].IB, n * 8, cudaMemcpyDeviceToDevice);
-            cudaMemcpy(nw.req[p], w.req[p], sizeof(int2) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
-            cudaMemcpy(nw.req_d[p], w.req_d[p], sizeof(double4) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
+            cudaMemcpy(nw.req[p], w.req[p], sizeof(FanReq) * (size_t)ws->req_cap, cudaMemcpyDeviceToDevice);
         }
         e = cudaDeviceSynchronize();
         if (e) { fresh.release(); return set_error(PCH_ERR_CUDA, "pool growth copy: %s", cudaGetErrorString(e)); }
@@ -1510,7 +1527,7 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
         const DevMesh& dm = meshes[i]->dm;
         Inst& I = hinst[i];
         I.rec = dm.rec; I.vstart = dm.vstart; I.vlist = dm.vlist; I.vphi = dm.vphi; I.vtheta = dm.vtheta;
-        I.hang = dm.hang; I.vflag = dm.vflag;
+        I.hang = dm.hang; I.vflag = dm.vflag; I.vrot = dm.vrot; I.vtrot = dm.vtrot;
         I.g = ws->g_all + gofs[i];
         I.ang = ws->ang_all + aofs[i];
         I.stamp = ws->stamp_all + gofs[i];
