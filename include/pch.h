@@ -92,12 +92,16 @@ typedef struct {
 } pch_options;
 
 enum {
-    PCH_FLAG_NO_TRIM = 1,     /* skip the per-edge trimming of Step 4 */
+    PCH_FLAG_NO_TRIM = 1,     /* with PCH_FLAG_EDGE_SORT: skip the per-edge trimming of Step 4 */
     PCH_FLAG_FULL_FAN = 2,    /* pseudo-source fans over the whole one-ring instead of the
                                  fanned area of Fig. `fig:propagation`(c) */
     PCH_FLAG_TRACE = 4,       /* record per-iteration controller features (pch_trace_fetch) */
-    PCH_FLAG_PROFILE = 8      /* host-driven loop with CUDA events around every phase
+    PCH_FLAG_PROFILE = 8,     /* host-driven loop with CUDA events around every phase
                                  (pch_stats.ms_phase); slower, for measurement only */
+    PCH_FLAG_EDGE_SORT = 16   /* organise new windows by (instance, half-edge) with a radix
+                                 sort and drop windows another window on the same edge
+                                 dominates (per-edge trimming); by default they are only
+                                 grouped by instance (Algorithm 3's gap-free copy) */
 };
 
 /* Per-call statistics (the columns of Table `tab:speedup`: time, windows, peak windows). */

@@ -1,7 +1,8 @@
 // Data organisation (Step 3 of Section 4.2, Algorithm 3): the windows a propagation
-// step produced are gathered into a gap-free pool, here in the order of their edge key
-// (instance key base + half-edge id) so that windows on one edge are adjacent for the
-// per-edge trimming of Step 4 and the next propagation reads edge records in order.
+// step produced are gathered into a gap-free pool, grouped by instance (so that the
+// append and the selection see one instance per warp), or on request in the order of
+// their edge key (instance key base + half-edge id) so that windows on one edge are
+// adjacent for the per-edge trimming of Step 4.  A single instance needs no sort.
 //
 // Hand-written stable LSD radix sort of (32-bit key, 32-bit index) pairs, 8-bit digits.
 // The element count n lives in device memory, so every launch has a fixed grid (graph
@@ -42,7 +43,8 @@ __device__ __forceinline__ int rs_active(int n) {
 __device__ __forceinline__ unsigned rs_key(const RsIn& in, int i) {
     if (in.keys) return in.keys[i];
     int h = in.he[i];
-    return h < 0 ? ~0u : (unsigned)(in.insts[in.inst[i]].keybase + h);
+    if (h < 0) return ~0u;
+    return in.by_edge ? (unsigned)(in.insts[in.inst[i]].keybase + h) : (unsigned)in.inst[i];
 }
 
 __global__ void __launch_bounds__(kRsThreads) k_rs_hist(RsIn in, const int* n_ptr, int cap, int shift, int* hist) {
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kRsThreads) k_rs_scatter(RsIn in, unsigned* __
 
 // Sort the child arena by edge key.  Leaves the sorted (key, index) pairs in
 // key_buf[r] / val_buf[r] and returns r.
-int launch_sort_children(const WinSoA& arena, const Inst* insts, const int* n_ptr, int cap, int key_bits,
+int launch_sort_children(const WinSoA& arena, const Inst* insts, const int* n_ptr, int cap, int key_bits, int by_edge,
                          unsigned* key_buf[2], int* val_buf[2], int* hist, int blocks, cudaStream_t s) {
     int passes = (key_bits + kRsDigitBits - 1) / kRsDigitBits;
     if (passes < 1) passes = 1;
@@ -145,6 +147,7 @@ int launch_sort_children(const WinSoA& arena, const Inst* insts, const int* n_pt
         in.he = arena.he;
         in.inst = arena.inst;
         in.insts = insts;
+        in.by_edge = by_edge;
         if (src >= 0) {
             in.keys = key_buf[src];
             in.vals = val_buf[src];

@@ -15,9 +15,10 @@ struct RsIn {
     const int* he;
     const int* inst;
     const Inst* insts;
+    int by_edge;    // key = instance key base + half-edge; else the instance
 };
 
-int launch_sort_children(const WinSoA& arena, const Inst* insts, const int* n_ptr, int cap, int key_bits,
+int launch_sort_children(const WinSoA& arena, const Inst* insts, const int* n_ptr, int cap, int key_bits, int by_edge,
                          unsigned* key_buf[2], int* val_buf[2], int* hist, int blocks, cudaStream_t s);
 int sort_kernels_per_pass();
 

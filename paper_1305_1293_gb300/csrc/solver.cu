@@ -965,13 +965,14 @@ __global__ void __launch_bounds__(256) k_append(Work w, const unsigned* __restri
     constexpr int kTrimReach = 4;
     for (int base = blockIdx.x * blockDim.x; base < n; base += gridDim.x * blockDim.x) {
         const int i = base + threadIdx.x;
-        unsigned k = i < n ? keys[i] : ~0u;
+        // without a sort (keys == nullptr) the arena is appended in its own order
+        unsigned k = i < n ? (keys ? keys[i] : (w.arena.he[i] < 0 ? ~0u : 0u)) : ~0u;
         bool keep = k != ~0u;
         int he = 0, inst = 0, src = -1;
         double d = 0, A = 0, B = 0, px = 0, py = 0, key = 0, IA = 0, IB = 0;
         int trimmed = 0;
         if (keep) {
-            load_win(w.arena, vals[i], he, inst, d, A, B, px, py, key, src, IA, IB);
+            load_win(w.arena, keys ? vals[i] : i, he, inst, d, A, B, px, py, key, src, IA, IB);
             const Inst& I = w.inst[inst];
             const HERec R = I.rec[he];
             // re-filter against the distances after this iteration's events (the window
@@ -1258,7 +1259,7 @@ static int grid_for(int blocks_per_sm) { return sm_count() * blocks_per_sm; }
 // Kernels one iteration launches (for pch_stats.kernel_launches).
 static int kernels_per_iteration(const SolveCfg& cfg) {
     int passes = (cfg.key_bits + kRsDigitBits - 1) / kRsDigitBits;
-    return 6 + (cfg.stride_T > 0 ? 1 : 0) + sort_kernels_per_pass() * (passes < 1 ? 1 : passes);
+    return 6 + (cfg.stride_T > 0 ? 1 : 0) + sort_kernels_per_pass() * passes;
 }
 
 // Launch one iteration (all phases).  With `ev` (7 events) the phase boundaries are
@@ -1288,10 +1289,12 @@ static cudaError_t launch_iteration(Workspace* ws, cudaStream_t s, const SolveCf
     if (ev) cudaEventRecord(ev[3], s);
     unsigned* kb[2] = {w.sort_key[0], w.sort_key[1]};
     int* vb[2] = {w.sort_val[0], w.sort_val[1]};
-    int par = launch_sort_children(w.arena, w.inst, &w.cnt->n_child, w.arena_cap, cfg.key_bits, kb, vb, w.sort_hist,
+    const int par = cfg.key_bits == 0 ? -1 :
+        launch_sort_children(w.arena, w.inst, &w.cnt->n_child, w.arena_cap, cfg.key_bits, cfg.edge_sort, kb, vb, w.sort_hist,
                                    w.sort_blocks, s);
     if (ev) cudaEventRecord(ev[4], s);
-    k_append<<<grid_for(4), tpb, 0, s>>>(w, kb[par], vb[par], cfg.trim);
+    k_append<<<grid_for(4), tpb, 0, s>>>(w, par >= 0 ? kb[par] : nullptr, par >= 0 ? vb[par] : nullptr,
+                                          cfg.trim && cfg.edge_sort);
     if (ev) cudaEventRecord(ev[5], s);
     k_finish<<<1, 1, 0, s>>>(w, h, use_cond, cfg.max_iters);
     if (ev) cudaEventRecord(ev[6], s);
@@ -1455,8 +1458,17 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     cfg.hops = (opt && opt->hops > 0) ? opt->hops : default_hops();
     cfg.tail_cut = default_tail_cut();
     cfg.unroll = 2;
-    int bits = 1;
-    while ((1LL << bits) <= total_keys) ++bits;   // invalid key ~0u must exceed all valid keys
+    // Step 3 organises the new windows into a gap-free pool; they are grouped by instance
+    // (one 8-bit radix pass for up to 256 instances, none for one), or with
+    // PCH_FLAG_EDGE_SORT ordered by (instance, half-edge) for the per-edge trimming
+    cfg.edge_sort = (opt && (opt->flags & PCH_FLAG_EDGE_SORT)) ? 1 : 0;
+    int bits = 0;
+    if (cfg.edge_sort) {
+        bits = 1;
+        while ((1LL << bits) <= total_keys) ++bits;   // invalid key ~0u must exceed all valid keys
+    } else {
+        while ((1LL << bits) < n_inst) ++bits;
+    }
     cfg.key_bits = bits;
     cfg.mlp = nullptr;
     cfg.stride_T = cfg.stride_m = 0;

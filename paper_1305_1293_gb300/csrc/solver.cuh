@@ -18,6 +18,7 @@ struct SolveCfg {
     int prop_blocks_per_sm;
     int key_bits;
     int trim;
+    int edge_sort;          // sort new windows by (instance, half-edge) instead of by instance
     int unroll;
     int full_fan;
     int profile;

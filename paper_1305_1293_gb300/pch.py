@@ -18,7 +18,7 @@ PCH_OK, PCH_ERR_INVALID_ARG, PCH_ERR_NONMANIFOLD, PCH_ERR_DEGENERATE = 0, 1, 2, 
 PCH_ERR_OOM, PCH_ERR_CUDA, PCH_ERR_CAPACITY, PCH_ERR_TIMEOUT = 4, 5, 6, 7
 CONTROL_PLAIN, CONTROL_LEARNED, CONTROL_STRIDED = 0, 1, 2
 LOOP_GRAPH, LOOP_HOST = 0, 1
-FLAG_NO_TRIM, FLAG_FULL_FAN, FLAG_TRACE, FLAG_PROFILE = 1, 2, 4, 8
+FLAG_NO_TRIM, FLAG_FULL_FAN, FLAG_TRACE, FLAG_PROFILE, FLAG_EDGE_SORT = 1, 2, 4, 8, 16
 PHASES = ("select", "propagate", "fan", "sort", "append", "control")
 
 _STATUS = {1: "INVALID_ARG", 2: "NONMANIFOLD", 3: "DEGENERATE", 4: "OOM", 5: "CUDA", 6: "CAPACITY", 7: "TIMEOUT"}

@@ -157,9 +157,10 @@ def test_unknown_control_rejected(pch):
     mesh.close()
 
 
-@pytest.mark.parametrize("flags", ["NO_TRIM", "FULL_FAN", "NO_TRIM|FULL_FAN"])
+@pytest.mark.parametrize("flags", ["EDGE_SORT", "EDGE_SORT|NO_TRIM", "FULL_FAN", "EDGE_SORT|FULL_FAN"])
 def test_variants_same_result(pch, oracle_lib, flags):
-    """Trimming and the fanned-area restriction remove only useless windows."""
+    """Per-edge trimming (after the edge sort) and the fanned-area restriction remove only
+    useless windows."""
     fl = 0
     for f in flags.split("|"):
         fl |= getattr(pch, "FLAG_" + f)
