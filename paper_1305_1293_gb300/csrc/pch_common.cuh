@@ -9,10 +9,14 @@
 namespace pch {
 
 // ---- tolerances (same values, independently written, as the CPU oracle) -------------
-// "A = v0", "B = v1" and vertex occupancy are decided within kEpsSnap * |e|.
-constexpr double kEpsSnap = 1e-12;
+// "A = v0", "B = v1" and vertex occupancy are decided within kEpsSnap * |e| (2^-40,
+// about 9.1e-13, a power of two so that the product is an exponent shift).
+constexpr double kEpsSnap = 0x1p-40;
 // Windows narrower than kEpsTiny * |e| are dropped (Section 5.3 drops tiny windows).
-constexpr double kEpsTiny = 1e-12;
+constexpr double kEpsTiny = 0x1p-40;
+// kEpsSnap in units in the last place: B is at v1 when within 4096 ulp of |e| (between
+// 2^-41 and 2^-40 of it, by where |e| falls in its binade).
+constexpr long long kSnapUlps = 4096;
 // A filter removes a window only when it is worse by more than this relative margin.
 constexpr double kDomRel = 1e-12;
 
@@ -36,8 +40,8 @@ constexpr int kHidden = 64;
 struct __align__(16) HERec {
     double L, xc, yc;      // edge length and apex position
     double L1, L2;         // |v1 v2|, |v2 v0|
-    double iL1, iL2;       // reciprocals of L1, L2
-    double iLq;            // 2^kAngleXBits / L: crossing position -> angle_split units
+    double uR[2];          // unit vector of v2 -> v1 (the right child's edge) in this frame
+    double uL[2];          // unit vector of v0 -> v2 (the left child's edge)
     int tw1;               // twin of next(h) = (v2 -> v1) in the neighbour: right child's edge
     int tw2;               // twin of prev(h) = (v0 -> v2) in the neighbour: left child's edge
     unsigned v0, v1, v2;   // vertex ids | kPseudoBit
@@ -198,5 +202,12 @@ __device__ __forceinline__ bool lt_s(double x, double y) { return sbits(x) < sbi
 __device__ __forceinline__ bool le_s(double x, double y) { return sbits(x) <= sbits(y); }
 __device__ __forceinline__ bool gt0_s(double x) { return sbits(x) > 0; }    // x > 0 (NaN: by sign)
 __device__ __forceinline__ bool ge0_s(double x) { return sbits(x) >= 0; }   // x >= +0
+
+// x * 2^-40 for a positive x by its exponent field (no FP64 instruction); x at or below
+// 2^-900 takes the multiplication.
+__device__ __forceinline__ double times_eps(double x) {
+    const long long b = sbits(x);
+    return b > 0x07B0000000000000ll ? __longlong_as_double(b - (40ll << 52)) : x * kEpsSnap;
+}
 
 }  // namespace pch

@@ -49,6 +49,7 @@ __device__ __forceinline__ unsigned long long pack_angle(double D, double xq) {
 }
 // kEpsSnap in angle_split units (the snap tolerance kEpsSnap * L times 2^24 / L).
 constexpr double kSplitTol = kEpsSnap * (double)(1 << kAngleXBits);
+constexpr double kAngleScale = (double)(1 << kAngleXBits);
 
 struct WarpScan {
     int excl, total;
@@ -398,15 +399,26 @@ struct ChildOut {
 // in the parent frame) meets the child's line O + s u where
 //   s = cross(I - O, D) / cross(u, D),   I + t D with t = cross(I - O, u) / cross(u, D),
 // and cross(I - O, u) = -Ipy.  Inputs: upy = ux py, rpy = rx py, (rx, ry) = I - O.
-// Returns s and |I X| = t |D|; a hit outside [0, Lc] (or a ray that does not cross) is
-// clamped to the nearer end with |I X| recomputed there.
+// Returns s and |I X| = t |D|.  A hit within 2^-40 Lc beyond an end (rounding, for a
+// parent window that ends on a vertex) is clamped to that end with |I X| kept; a hit
+// further outside [0, Lc] (or a ray that does not cross) is clamped to the nearer end
+// with |I X| recomputed there.
 __device__ __forceinline__ void ray_hit(double dx, double ID, double ux, double uy, double ry, double upy, double rpy,
                                         double py, double Ipx, double Ipy, double Lc, double& xh, double& IX) {
     const double den = -fma(uy, dx, upy);   // cross(u, D)
-    const double r = rcp_nr(den);
+    const double r = rcp_nr(den);           // full precision: |I X| compounds along a lineage
     xh = -fma(ry, dx, rpy) * r;             // cross(I - O, D) / cross(u, D)
     IX = (-Ipy * r) * ID;
     if (!gt0_s(den) || !(ge0_s(xh) && le_s(xh, Lc))) {
+        const long long xb = sbits(xh);
+        if (gt0_s(den) && xb < 0 && (xb & 0x7fffffffffffffffll) <= sbits(times_eps(Lc))) {
+            xh = 0.0;
+            return;
+        }
+        if (gt0_s(den) && xb > sbits(Lc) && xb - sbits(Lc) <= kSnapUlps) {
+            xh = Lc;
+            return;
+        }
         xh = gt0_s(den) ? (lt_s(xh, 0.0) ? 0.0 : (lt_s(Lc, xh) ? Lc : xh))
                         : (gt0_s(fma(ux, dx, -uy * py)) ? Lc : 0.0);   // dot(u, D) > 0: towards Lc
         if (!(xh == xh)) xh = 0.0;
@@ -479,15 +491,15 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
             // a window that must go, and they are skipped.
             prop = true;
             const double py2 = py * py;
-            const double tol = kEpsSnap * L;
-            const double tiny = kEpsTiny == kEpsSnap ? tol : kEpsTiny * L;
+            const double tol = times_eps(L);
+            const double tiny = tol;
             // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
             if (le_s(A, tol)) {
                 double D0 = d + (sbits(A) == 0 ? IA : sqrt(px * px + py2));
                 if (vertex_event(I, R.v0, D0, g0))   // the ray arrives at v0 from I (h's frame)
                     push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v0 & ~kPseudoBit, D0, h, px, py);
             }
-            if (le_s(L - tol, B)) {
+            if (sbits(L) - sbits(B) <= kSnapUlps) {
                 double q = L - px;
                 double D1 = d + (sbits(B) == sbits(L) ? IB : sqrt(q * q + py2));
                 if (vertex_event(I, R.v1, D1, g1))   // at v1, in the frame of twin(h) = (v1 -> v0)
@@ -502,7 +514,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
             if (occ) {
                 const double xs = px + num * rcp_nr(den);
                 const double xcl = lt_s(xs, A) ? A : (lt_s(B, xs) ? B : xs);
-                const double xq = xs * R.iLq;
+                const double xq = xs * rcp_nr(L) * kAngleScale;
                 const double dx = xc - px, dy = yc - py;
                 Iv2 = sqrt_nr(dx * dx + dy * dy);
                 const double D2 = d + Iv2;
@@ -526,7 +538,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                     // the ray arrives at v2 inside face(h); direction to I in the frame of
                     // prev(h) = (v2 -> v0), whose axis is (-xc, -yc) / L2
                     const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
-                    const double ux = -xc * R.iL2, uy = -yc * R.iL2, ex = px - xc, ey = py - yc;
+                    const double ux = -R.uL[0], uy = -R.uL[1], ex = px - xc, ey = py - yc;
                     push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v2 & ~kPseudoBit, D2, hp,
                              ex * ux + ey * uy, ux * ey - uy * ex);
                 }
@@ -565,10 +577,9 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                 }
                 // both sides as one select-driven path (a warp holds left and right children)
                 const double Lc = rt ? R.L1 : R.L2;
-                const double sc = rt ? R.iL1 : R.iL2;
                 const double ox = rt ? xc : 0.0, oy = rt ? yc : 0.0;
-                const double ux = (rt ? L - xc : xc) * sc;
-                const double uy = (rt ? -yc : yc) * sc;
+                const double ux = rt ? R.uR[0] : R.uL[0];
+                const double uy = rt ? R.uR[1] : R.uL[1];
                 const double rx = px - ox, ry = py - oy;
                 const double Ipx = fma(rx, ux, ry * uy), Ipy = fma(ux, ry, -(uy * rx));
                 const double upy = ux * py, rpy = rx * py;
@@ -587,7 +598,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                 } else {
                     ray_hit(bx, IB, ux, uy, ry, upy, rpy, py, Ipx, Ipy, Lc, b, IBc);
                 }
-                if (!lt_s(kEpsTiny * Lc, b - a)) continue;
+                if (!lt_s(times_eps(Lc), b - a)) continue;
                 // Xin-Wang filter (Fig. `fig:filter`(b)) on the new window: against its
                 // start and end vertices (right child: v2, v1; left child: v0, v2), and
                 // against the vertex of the parent edge off the child's edge, tested at the
@@ -781,7 +792,7 @@ __device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) {   // a * co
 // Where the ray from the apex v of o's face along z (relative to the direction
 // v -> start(o), any length) meets o: distance from start(o), clamped to [0, L].
 __device__ __forceinline__ double fan_hit(const HERec& Ro, double2 z) {
-    const double ux = -Ro.xc * Ro.iL2, uy = -Ro.yc * Ro.iL2;   // v -> start(o), unit
+    const double ux = -Ro.uL[0], uy = -Ro.uL[1];                // v -> start(o), unit
     const double dx = fma(ux, z.x, -uy * z.y), dy = fma(ux, z.y, uy * z.x);
     if (!(dy < 0.0)) return dx > 0.0 ? Ro.L : 0.0;             // parallel to o or turned away
     const double s = fma(-Ro.yc * dx, rcp_nr(dy), Ro.xc);
@@ -933,7 +944,7 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
             const double px = Lo - Ro.xc, py = -Ro.yc;
             const double IA = sqrt_nr(fma(A - px, A - px, py * py)), IB = sqrt_nr(fma(B - px, B - px, py * py));
             const double ga = ldg_dist(I.g, Ro.v0 & ~kPseudoBit), gb = ldg_dist(I.g, Ro.v1 & ~kPseudoBit);
-            if (!(B - A > kEpsTiny * Lo) || dominated(D + IB, gb + B) || dominated(D + IA, ga + (Lo - A))) {
+            if (!(B - A > times_eps(Lo)) || dominated(D + IB, gb + B) || dominated(D + IA, ga + (Lo - A))) {
                 w.arena.he[slot] = -1;
                 continue;
             }
@@ -1432,13 +1443,13 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         // algorithmic FP64 operations of k_propagate (add, sub, mul, div, sqrt = 1; fma = 2),
         // counted per code path of propagate_window: a window taken from the work list 7
         // (2 offsets, 5 for the endpoint filter), a chained window 2 (its filter was its
-        // parent's child filter), a window that passed +10 (snap tolerance and occupancy
-        // test), an occupied one +14 (crossing point, |I v2|, event distance), a child
-        // +32 (frame change 13, width test 2, child filter 16, key 1) plus 8 per ray
+        // parent's child filter), a window that passed +9 (occupancy test), an occupied
+        // one +15 (crossing point and its angle_split position, |I v2|, event distance),
+        // a child +28 (frame change 10, width 1, child filter 16, key 1) plus 8 per ray
         // intersected (two per child, one when the window occupies v2)
         const unsigned long long fresh = c.examined > c.chained ? c.examined - c.chained : 0ull;
-        stats->prop_fp64_ops = (int64_t)(7ull * fresh + 2ull * c.chained + 10ull * c.propagated +
-                                         14ull * c.occupied + 32ull * c.children + 8ull * c.rays);
+        stats->prop_fp64_ops = (int64_t)(7ull * fresh + 2ull * c.chained + 9ull * c.propagated +
+                                         15ull * c.occupied + 28ull * c.children + 8ull * c.rays);
         for (int p = 0; p < 6; ++p) stats->ms_phase[p] = phase_ms[p];
     }
     return PCH_OK;
@@ -1795,6 +1806,7 @@ __global__ void k_selftest_math(const double* __restrict__ x, int n, unsigned lo
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double v = x[i];
         const long long a = __double_as_longlong(rcp_nr(v)), b = __double_as_longlong(1.0 / v);
+
         const long long c = __double_as_longlong(sqrt_nr(fabs(v))), d = __double_as_longlong(sqrt(fabs(v)));
         unsigned long long ur = (unsigned long long)(a > b ? a - b : b - a);
         unsigned long long us = (unsigned long long)(c > d ? c - d : d - c);
