@@ -40,8 +40,9 @@ constexpr int kHidden = 64;
 struct __align__(16) HERec {
     double L, xc, yc;      // edge length and apex position
     double L1, L2;         // |v1 v2|, |v2 v0|
-    double uR[2];          // unit vector of v2 -> v1 (the right child's edge) in this frame
-    double uL[2];          // unit vector of v0 -> v2 (the left child's edge)
+    double iL1, iL2;       // reciprocals of L1, L2
+    double iLq;            // 2^kAngleXBits / L: crossing position -> angle_split units
+    double pad;
     int tw1;               // twin of next(h) = (v2 -> v1) in the neighbour: right child's edge
     int tw2;               // twin of prev(h) = (v0 -> v2) in the neighbour: left child's edge
     unsigned v0, v1, v2;   // vertex ids | kPseudoBit

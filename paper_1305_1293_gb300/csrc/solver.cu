@@ -40,12 +40,15 @@ __device__ __forceinline__ double ldg_dist(const unsigned long long* g, unsigned
 // distance is rounded UP to 40 significant bits (so a stored value never understates the
 // window's distance) and the crossing position, given as xq = 2^24 x / L, floored to 24
 // bits.
+// Crossing position in angle_split units: floor(xq) clamped to [0, 2^24 - 1].
+__device__ __forceinline__ long long angle_pos(double xq) {
+    const long long q = __double2ll_rd(xq);
+    return q < 0 ? 0 : (q > (long long)kAngleXMask ? (long long)kAngleXMask : q);
+}
 __device__ __forceinline__ unsigned long long pack_angle(double D, double xq) {
     unsigned long long b = dbits(D);
     if (b & kAngleXMask) b = (b | kAngleXMask) + 1ull;
-    long long q = __double2ll_rd(xq);
-    q = q < 0 ? 0 : (q > (long long)kAngleXMask ? (long long)kAngleXMask : q);
-    return (b & ~kAngleXMask) | (unsigned long long)q;
+    return (b & ~kAngleXMask) | (unsigned long long)angle_pos(xq);
 }
 // kEpsSnap in angle_split units (the snap tolerance kEpsSnap * L times 2^24 / L).
 constexpr double kSplitTol = kEpsSnap * (double)(1 << kAngleXBits);
@@ -495,13 +498,13 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
             const double tiny = tol;
             // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
             if (le_s(A, tol)) {
-                double D0 = d + (sbits(A) == 0 ? IA : sqrt(px * px + py2));
+                double D0 = d + (sbits(A) == 0 ? IA : sqrt_nr(fma(px, px, py2)));
                 if (vertex_event(I, R.v0, D0, g0))   // the ray arrives at v0 from I (h's frame)
                     push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v0 & ~kPseudoBit, D0, h, px, py);
             }
             if (sbits(L) - sbits(B) <= kSnapUlps) {
                 double q = L - px;
-                double D1 = d + (sbits(B) == sbits(L) ? IB : sqrt(q * q + py2));
+                double D1 = d + (sbits(B) == sbits(L) ? IB : sqrt_nr(fma(q, q, py2)));
                 if (vertex_event(I, R.v1, D1, g1))   // at v1, in the frame of twin(h) = (v1 -> v0)
                     push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v1 & ~kPseudoBit, D1, R.twin, q, -py);
             }
@@ -514,7 +517,9 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
             if (occ) {
                 const double xs = px + num * rcp_nr(den);
                 const double xcl = lt_s(xs, A) ? A : (lt_s(B, xs) ? B : xs);
-                const double xq = xs * rcp_nr(L) * kAngleScale;
+                // angle_split position: xs in units of 2^-24 |e| (only the order of positions
+                // on one edge matters, so any fixed scale per edge will do)
+                const double xq = xs * R.iLq;
                 const double dx = xc - px, dy = yc - py;
                 Iv2 = sqrt_nr(dx * dx + dy * dy);
                 const double D2 = d + Iv2;
@@ -529,16 +534,17 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                     // loser: keep the child on its own side of the winner's ray, which
                     // crosses e in [q, q + 1] (angle_split units), widened by the snap
                     // tolerance
+                    // (positions compared after the same clamping the stored one had)
                     const long long q = (long long)(aw & kAngleXMask);
-                    left = __double2ll_rd(xq + kSplitTol) < q;
-                    right = __double2ll_rd(xq - kSplitTol) > q;
+                    left = angle_pos(xq + kSplitTol) < q;
+                    right = angle_pos(xq - kSplitTol) > q;
                     if (!left && !right) left = right = true;
                 }
                 if (vertex_event(I, R.v2, D2, g2)) {
                     // the ray arrives at v2 inside face(h); direction to I in the frame of
                     // prev(h) = (v2 -> v0), whose axis is (-xc, -yc) / L2
                     const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
-                    const double ux = -R.uL[0], uy = -R.uL[1], ex = px - xc, ey = py - yc;
+                    const double ux = -xc * R.iL2, uy = -yc * R.iL2, ex = px - xc, ey = py - yc;
                     push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v2 & ~kPseudoBit, D2, hp,
                              ex * ux + ey * uy, ux * ey - uy * ex);
                 }
@@ -578,8 +584,9 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                 // both sides as one select-driven path (a warp holds left and right children)
                 const double Lc = rt ? R.L1 : R.L2;
                 const double ox = rt ? xc : 0.0, oy = rt ? yc : 0.0;
-                const double ux = rt ? R.uR[0] : R.uL[0];
-                const double uy = rt ? R.uR[1] : R.uL[1];
+                const double sc = rt ? R.iL1 : R.iL2;
+                const double ux = (rt ? L - xc : xc) * sc;
+                const double uy = (rt ? -yc : yc) * sc;
                 const double rx = px - ox, ry = py - oy;
                 const double Ipx = fma(rx, ux, ry * uy), Ipy = fma(ux, ry, -(uy * rx));
                 const double upy = ux * py, rpy = rx * py;
@@ -792,7 +799,7 @@ __device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) {   // a * co
 // Where the ray from the apex v of o's face along z (relative to the direction
 // v -> start(o), any length) meets o: distance from start(o), clamped to [0, L].
 __device__ __forceinline__ double fan_hit(const HERec& Ro, double2 z) {
-    const double ux = -Ro.uL[0], uy = -Ro.uL[1];                // v -> start(o), unit
+    const double ux = -Ro.xc * Ro.iL2, uy = -Ro.yc * Ro.iL2;   // v -> start(o), unit
     const double dx = fma(ux, z.x, -uy * z.y), dy = fma(ux, z.y, uy * z.x);
     if (!(dy < 0.0)) return dx > 0.0 ? Ro.L : 0.0;             // parallel to o or turned away
     const double s = fma(-Ro.yc * dx, rcp_nr(dy), Ro.xc);

@@ -340,3 +340,61 @@ def test_fast_reciprocal_and_sqrt_within_few_ulp(pch):
     x = np.concatenate([x, [1.0, 2.0, 0.5, 3.0, 1e-31, 1e31, 7.0e-300]])
     ur, us = pch.selftest_math(torch.from_numpy(x).cuda())
     assert ur <= 2 and us <= 2, (ur, us)
+
+
+def _sampled_batch_checks(pch, oracle_lib, meshes, inst, outs, n_near, n_oracle, upper_every=0):
+    """Invariants on every vertex of every instance of a batched solve, at the parity bar
+    (1e-9 relative: the bound the workload sets for every distance), and the oracle on
+    the n_near vertices nearest the source of n_oracle instances spread over the batch."""
+    step = max(1, len(inst) // max(1, n_oracle))
+    for j, ((mi, s), got) in enumerate(zip(inst, outs)):
+        m = meshes[mi]
+        assert got[s] == 0.0 and np.all(np.isfinite(got)), (j, int(np.sum(~np.isfinite(got))))
+        chord = np.linalg.norm(m.vertices - m.vertices[s], axis=1)
+        assert np.all(got >= chord * (1 - TOL)), (j, float(np.min(got / np.maximum(chord, 1e-300))))
+        e = np.concatenate([m.faces[:, [0, 1]], m.faces[:, [1, 2]]])
+        le = np.linalg.norm(m.vertices[e[:, 0]] - m.vertices[e[:, 1]], axis=1)
+        ratio = np.abs(got[e[:, 0]] - got[e[:, 1]]) / le
+        assert np.all(ratio <= 1 + TOL), (j, float(np.max(ratio)))
+        if upper_every and j % upper_every == 0:
+            assert np.all(got <= _edge_graph_upper(m, s) * (1 + TOL))
+        if j % step == 0:
+            near = np.argsort(got)[1:1 + n_near].astype(np.int32)
+            ref, _ = oracle_lib.geodesic(m.vertices, m.faces, s, targets=near)
+            assert max_rel(got[near], ref[near]) < TOL, (j, s)
+
+
+def test_full_batch_256_meshes(pch, oracle_lib):
+    """The 256-mesh workload at full size in one batched solve (plain control with the
+    tuned chaining), sampled against the oracle on 16 instances."""
+    meshes, srcs = mg.workload("batch", "full")
+    hs = [pch.Mesh(m.vertices, m.faces) for m in meshes]
+    inst = [(i, int(s[0])) for i, s in enumerate(srcs)]
+    outs = pch.solve_batch([hs[i] for i, _ in inst], [s for _, s in inst], k=24576, hops=16, block=128)
+    _sampled_batch_checks(pch, oracle_lib, meshes, inst, outs, n_near=150, n_oracle=16, upper_every=32)
+    for h in hs:
+        h.close()
+
+
+def test_full_multisrc_64_sources(pch, oracle_lib):
+    """64 sources on the 100,820-face sphere as one batched solve, every field checked by
+    invariants and 8 of them against the oracle."""
+    meshes, srcs = mg.workload("multisrc", "full")
+    m = meshes[0]
+    h = pch.Mesh(m.vertices, m.faces)
+    inst = [(0, int(s)) for s in srcs[0]]
+    outs = pch.solve_batch([h] * len(inst), [s for _, s in inst], k=24576, hops=4, block=256)
+    _sampled_batch_checks(pch, oracle_lib, meshes, inst, outs, n_near=300, n_oracle=8, upper_every=16)
+    h.close()
+
+
+def test_full_large_32_sources(pch, oracle_lib):
+    """The 5,242,880-face sphere with 32 sources in one batched solve (the largest
+    workload), every field checked by invariants and 4 against the oracle."""
+    meshes, srcs = mg.workload("large", "full")
+    m = meshes[0]
+    h = pch.Mesh(m.vertices, m.faces)
+    inst = [(0, int(s)) for s in srcs[0]]
+    outs = pch.solve_batch([h] * len(inst), [s for _, s in inst], k=1 << 22, hops=64, block=64)
+    _sampled_batch_checks(pch, oracle_lib, meshes, inst, outs, n_near=200, n_oracle=4, upper_every=0)
+    h.close()
