@@ -246,7 +246,7 @@ def run_gpu(args):
             "parity_max_rel_err_sampled": parity,
             "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": achieved_tf,
                          "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_DERIVED,
-                         "traffic": None, "fp64_microbench_tflops": fp64_meas,
+                         "traffic": prop_traffic(), "fp64_microbench_tflops": fp64_meas,
                          "fp64_ops_per_launch": pst["prop_fp64_ops"] / max(1, prop_launches),
                          "fp64_ops_per_window": pst["prop_fp64_ops"] / max(1, pst["windows_propagated"]),
                          "launches": prop_launches,
@@ -270,6 +270,22 @@ def run_gpu(args):
 
 
 HBM_PEAK_GBS = 6699.8   # measured STREAM-style copy bandwidth of a GB300 (MEASURED_PEAKS.json hbm_gbs)
+
+# DRAM bytes (read + write) per k_propagate launch on this workload, from the ncu launch
+# list in profiles/terrain512_launch_list.md, valid only for the kernel sources it was
+# taken on (their hash); any change of them reports null until the list is taken again.
+PROP_TRAFFIC = {"sources_sha256_16": "0d616c4973624cd2", "bytes_per_launch": 26.80e6}
+PROP_SOURCES = ("paper_1305_1293_gb300/csrc/solver.cu", "paper_1305_1293_gb300/csrc/pch_common.cuh",
+                "paper_1305_1293_gb300/csrc/fastmath.cuh")
+
+
+def prop_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in PROP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return PROP_TRAFFIC["bytes_per_launch"] if h.hexdigest()[:16] == PROP_TRAFFIC["sources_sha256_16"] else None
 
 
 def phase_rooflines(pst, passes):
