@@ -96,6 +96,28 @@ def oracle_sample(m, s, budget_s: float = 20.0):
     return st["propagated"] / dt, dt, st["propagated"]
 
 
+def cpu_pch_sample(k: int = 24576):
+    """The paper's CPU PCH (Section 6: rounds of the k nearest windows, unordered) against
+    the sequential priority-queue oracle on the reduced terrain of the same family (48 x 48,
+    4,608 faces, whole field): the window overhead of unordered rounds, which the GPU path
+    shares, and the CPU rate."""
+    import oracle
+    from paper_1305_1293_gb300 import meshgen as mg
+    meshes, srcs = mg.workload("terrain", "small")
+    m, s = meshes[0], int(srcs[0][0])
+    t = time.perf_counter()
+    ref, st_ich = oracle.geodesic(m.vertices, m.faces, s)
+    t_ich = time.perf_counter() - t
+    t = time.perf_counter()
+    d, st_pch = oracle.cpu_pch(m.vertices, m.faces, s, k)
+    t_pch = time.perf_counter() - t
+    return {"mesh": "terrain 48 x 48 (4,608 F), whole field", "k": k, "cores": 1,
+            "ich_windows": st_ich["propagated"], "cpu_pch_windows": st_pch["propagated"],
+            "window_ratio": st_pch["propagated"] / max(1, st_ich["propagated"]), "rounds": st_pch["rounds"],
+            "ich_s": t_ich, "cpu_pch_s": t_pch, "cpu_pch_windows_per_s": st_pch["propagated"] / max(t_pch, 1e-9),
+            "max_rel_diff": float(np.max(np.abs(d - ref) / np.maximum(ref, 1e-300)))}
+
+
 def run_reference(args):
     ws, rank, _ = _dist_env()
     if rank != 0:
@@ -226,6 +248,7 @@ def run_gpu(args):
         ref, _ = oracle.geodesic(m.vertices, m.faces, s, targets=near.astype(np.int32))
         parity = float(np.max(np.abs(got[near] - ref[near]) / ref[near]))
         cpu_v, cpu_dt, cpu_w = oracle_sample(m, s)
+        cpu_pch = cpu_pch_sample()
         clocks = clk.summary()
         st0 = stats[-1]
         line = {
@@ -258,6 +281,7 @@ def run_gpu(args):
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": sum(e2e_ms) / len(e2e_ms),
                     "h2d_bytes_per_step": int(m.vertices.nbytes + m.faces.nbytes),
                     "d2h_bytes_per_step": int(8 * m.nv)},
+            "cpu_pch_baseline": cpu_pch,
             "gpu_launches": int(sum(st["kernel_launches"] for st in stats)),
             "clocks": clocks,
         }
