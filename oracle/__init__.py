@@ -2,8 +2,9 @@
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU-baseline leg may
 import this package.  It wraps ``ich_oracle.cpp`` (sequential FP64 Chen-Han/Xin-Wang,
-Algorithm 2 of the paper, and the sequential CPU PCH variant of Section 6) and ``mlp_oracle.py`` (FP64 reference of the selection
-controller's network).  It shares no code with the CUDA path.
+Algorithm 2 of the paper, the sequential CPU PCH variant of Section 6, and geodesic paths
+traced back along the window sequence of Section 4.4) and ``mlp_oracle.py`` (FP64
+reference of the selection controller's network).  It shares no code with the CUDA path.
 """
 from __future__ import annotations
 
@@ -45,6 +46,11 @@ def _declare(lib):
     lib.oracle_cpu_pch.restype = ctypes.c_int
     lib.oracle_cpu_pch.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
                                    ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.oracle_trace_paths.restype = ctypes.c_int
+    lib.oracle_trace_paths.argtypes = [
+        ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int,
+        ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
     lib.oracle_vertex_angles.restype = ctypes.c_int
     lib.oracle_vertex_angles.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                          ctypes.c_void_p, ctypes.c_void_p]
@@ -114,6 +120,54 @@ def cpu_pch(vertices, faces, source: int, k: int, *, flags: int = 0, lib=None):
     if rc != 0:
         raise OracleError(f"oracle_cpu_pch failed with code {rc}")
     return out, _stats(stats)
+
+
+def trace_paths(vertices, faces, source=None, *, targets, face=None, bary=None, sources=None,
+                max_points: int = 1 << 16, lib=None):
+    """Geodesic paths from the source(s) to each target, from the window sequence that
+    gave the target its distance (Section 4.4) and the straight unfolded segments of
+    Section 3's path structure.  Returns (dist[V], paths): paths[i] is None if the chain
+    was broken, else a tuple (kind, id, t0, t1) of arrays, target first: kind 0 a vertex,
+    1 a point on half-edge id (3 f + i, corner i to corner i + 1 of face f) at fraction
+    t0 from its start, 2 the face-point source in face id (barycentric t0, t1 of corners
+    1 and 2).  An unreachable target has an empty path."""
+    lib = lib or _load()
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    f = np.ascontiguousarray(faces, dtype=np.int32)
+    t = np.ascontiguousarray(targets, dtype=np.int32)
+    nt = int(t.shape[0])
+    out = np.empty(v.shape[0], dtype=np.float64)
+    b = np.zeros(3, dtype=np.float64)
+    srcs = np.zeros(1, dtype=np.int32)
+    if sources is not None:
+        kind, sv, sf = 2, 0, 0
+        srcs = np.ascontiguousarray(sources, dtype=np.int32)
+    elif face is not None:
+        kind, sv, sf = 1, 0, int(face)
+        b = np.ascontiguousarray(bary, dtype=np.float64)
+    else:
+        kind, sv, sf = 0, int(source), 0
+    kinds = np.zeros((max(nt, 1), max_points), dtype=np.int32)
+    ids = np.zeros_like(kinds)
+    t0 = np.zeros((max(nt, 1), max_points), dtype=np.float64)
+    t1 = np.zeros_like(t0)
+    n = np.zeros(max(nt, 1), dtype=np.int32)
+    rc = lib.oracle_trace_paths(v.shape[0], v.ctypes.data, f.shape[0], f.ctypes.data, kind, sv, sf, b.ctypes.data,
+                                int(srcs.shape[0]), srcs.ctypes.data, nt, t.ctypes.data, int(max_points),
+                                kinds.ctypes.data, ids.ctypes.data, t0.ctypes.data, t1.ctypes.data, n.ctypes.data,
+                                out.ctypes.data)
+    if rc != 0:
+        raise OracleError(f"oracle_trace_paths failed with code {rc}")
+    paths = []
+    for i in range(nt):
+        k = int(n[i])
+        if k < 0:
+            paths.append(None)
+            continue
+        if k > max_points:
+            raise OracleError(f"path {i} has {k} points, more than max_points={max_points}")
+        paths.append((kinds[i, :k].copy(), ids[i, :k].copy(), t0[i, :k].copy(), t1[i, :k].copy()))
+    return out, paths
 
 
 def vertex_angles(vertices, faces):

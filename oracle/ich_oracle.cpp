@@ -46,6 +46,7 @@ enum {
     ORDER_MASK = 3,
     NO_CH = 4,       // disable "one angle one split"
     NO_ICH = 8,      // disable the Xin-Wang filter
+    TRACE = 16,      // keep every window and each vertex's final event (geodesic paths)
 };
 
 inline bool dominated(double lhs, double rhs) { return lhs > rhs * (1.0 + kDomRel); }
@@ -115,6 +116,18 @@ int build_mesh(Mesh& m) {
 struct Window {
     double d, A, B, d0, d1;   // the paper's (d, A, B, d0, d1, e)
     int e;
+    // path bookkeeping (TRACE only): the pseudo-source vertex (-1: the face-point source),
+    // the window this one is a child of (-1: a fan or initial window) and its own index
+    int src = -1, parent = -1, id = -1;
+};
+
+// A distance event with where it came from (TRACE only): a window event (kind 0, the
+// window's index), a pseudo-source fan's event along a boundary edge (kind 1, from the
+// vertex src), or the corner of a face-point source's face (kind 2).
+struct Event {
+    int v;
+    double D;
+    int kind = -1, wid = -1, src = -1;
 };
 
 struct Entry {
@@ -170,11 +183,15 @@ struct Solver {
     std::vector<Entry> pool, batch;
     size_t bpos = 0;
     long long rounds = 0;
+    // TRACE: every window pushed, and per vertex the event that set its distance
+    std::vector<Window> hist;
+    std::vector<Event> prov;
 
     Solver(Mesh& mm, int fl, long long cap) : m(mm), flags(fl), max_windows(cap) {
         g.assign(m.nv, kInf);
         aD.assign(3 * m.nf, kInf);
         aX.assign(3 * m.nf, 0.0);
+        if (flags & TRACE) prov.assign(m.nv, Event{-1, kInf});
     }
 
     size_t qsize() const {
@@ -189,6 +206,10 @@ struct Solver {
         double L = m.len[w.e];
         Entry en{window_key(w, L), seq++, w};
         if (en.key > cap) return;
+        if (flags & TRACE) {
+            en.w.id = (int)hist.size();
+            hist.push_back(en.w);
+        }
         int order = flags & ORDER_MASK;
         if (order == ORDER_PQ) {
             pq.push(en);
@@ -259,18 +280,19 @@ struct Solver {
     // Pseudo-source fan at vertex v with distance D (Fig. `fig:propagation`(c)).  The
     // oracle creates a window on every edge opposite v (the whole one-ring): a superset
     // of the fanned area, sound because each window is a real path from the source.
-    void fan(int v, double D, std::vector<std::pair<int, double>>& work) {
+    void fan(int v, double D, std::vector<Event>& work) {
         for (int hv : m.out_he[v]) {
             int o = nxt(hv);          // edge (a -> b) opposite v in face(hv)
             int a = hfrom(m, o), b = hto(m, o);
             double va = m.len[hv], vb = m.len[nxt(o)];
             int t = m.twin[o];
             if (t < 0) {              // boundary: no face beyond, emit the endpoint events
-                work.push_back({a, D + va});
-                work.push_back({b, D + vb});
+                work.push_back(Event{a, D + va, 1, -1, v});
+                work.push_back(Event{b, D + vb, 1, -1, v});
                 continue;
             }
             Window w{D, 0.0, m.len[t], vb, va, t};   // on twin (b -> a): d0 = |vb|, d1 = |va|
+            w.src = v;
             // ICH filter on the new window: vs b at B (the a end), vs a at A (the b end);
             // the third vertex is v itself, i.e. the test reads D > g[v].
             if (ich_useless(D, 0.0, m.len[t], m.len[t], vb, va, b, a, v, true, va)) continue;
@@ -278,21 +300,29 @@ struct Solver {
         }
     }
 
-    void vertex_event(int v, double D, std::vector<std::pair<int, double>>& work) {
-        work.push_back({v, D});
+    void vertex_event(int v, double D, const Window& from, std::vector<Event>& work) {
+        work.push_back(Event{v, D, 0, from.id, from.src});
     }
 
     // Apply queued distance events in order; saddle / boundary vertices spawn fans.
-    void drain(std::vector<std::pair<int, double>>& work) {
+    void drain(std::vector<Event>& work) {
         while (!work.empty()) {
-            auto [v, D] = work.back();
+            const Event ev = work.back();
             work.pop_back();
             ++events;
-            if (D < g[v]) {
-                g[v] = D;
-                if (m.pseudo[v]) fan(v, D, work);
+            if (ev.D < g[ev.v]) {
+                g[ev.v] = ev.D;
+                if (flags & TRACE) prov[ev.v] = ev;
+                if (m.pseudo[ev.v]) fan(ev.v, ev.D, work);
             }
         }
+    }
+
+    // A child window keeps its parent's pseudo-source and remembers its parent.
+    static Window child(Window c, const Window& parent) {
+        c.src = parent.src;
+        c.parent = parent.id;
+        return c;
     }
 
     // Ray from I through (x, 0) meets the line through Q0 with unit direction u at
@@ -313,12 +343,12 @@ struct Solver {
         apex_xy(m, h, xc, yc);
         pseudo_xy(w, L, px, py);
         const double tol = kEpsSnap * L;
-        std::vector<std::pair<int, double>> work;
+        std::vector<Event> work;
 
         // Algorithm 2: A = v0 -> distance event (v0, d0 + d) (+ fan, applied in drain)
-        if (w.A <= tol) vertex_event(v0, w.d + w.d0, work);
+        if (w.A <= tol) vertex_event(v0, w.d + w.d0, w, work);
         // B = v1 -> distance event (v1, d1 + d)
-        if (w.B >= L - tol) vertex_event(v1, w.d + w.d1, work);
+        if (w.B >= L - tol) vertex_event(v1, w.d + w.d1, w, work);
 
         // Does w occupy v2?  Where the ray I -> v2 crosses e.
         double xs = px + (xc - px) * (-py) / (yc - py);
@@ -342,7 +372,7 @@ struct Solver {
                 else if (xs > aX[h] + tol) right = true;
                 else left = right = true;
             }
-            vertex_event(v2, D2, work);
+            vertex_event(v2, D2, w, work);
         } else if (xs < w.A) {
             right = true;                      // v2 lies left of the window: one child on (v2,v1)
         } else {
@@ -371,7 +401,7 @@ struct Solver {
                         // third vertex: v1 (parent edge {v0,v1}, shared vertex v0 -> test at A)
                         double v1A = std::hypot(ta * ux - L, ta * uy);
                         if (!ich_useless(w.d, ta, tb, Lc, IA, IB, v0, v2, v1, false, v1A))
-                            push(Window{w.d, ta, tb, w.d0, Iv2, c});
+                            push(child(Window{w.d, ta, tb, w.d0, Iv2, c}, w));
                     }
                 }
             }
@@ -397,7 +427,7 @@ struct Solver {
                         // third vertex: v0 (shared vertex v1 -> test at B)
                         double v0B = std::hypot(bx, by);
                         if (!ich_useless(w.d, ta, tb, Lc, IA, IB, v2, v1, v0, true, v0B))
-                            push(Window{w.d, ta, tb, Iv2, w.d1, c});
+                            push(child(Window{w.d, ta, tb, Iv2, w.d1, c}, w));
                     }
                 }
             }
@@ -414,6 +444,95 @@ struct Solver {
         double IA = std::hypot(w.A - px, py), IB = std::hypot(w.B - px, py);
         int v0 = hfrom(m, w.e), v1 = hto(m, w.e);
         return dominated(w.d + IB, g[v0] + w.B) || dominated(w.d + IA, g[v1] + (L - w.A));
+    }
+
+    // ---- geodesic paths (TRACE) ---------------------------------------------------
+    // A path point: a vertex (kind 0, id = vertex), a point on half-edge id at fraction t0
+    // from its start (kind 1), or the face-point source in face id with barycentric
+    // weights t0, t1 of the face's corners 1 and 2 (kind 2).
+    struct Pt {
+        int kind, id;
+        double t0, t1;
+    };
+    int sface = -1;
+    double sbary[3] = {0, 0, 0};
+
+    Pt face_point() const { return Pt{2, sface, sbary[1], sbary[2]}; }
+
+    // The geodesic path from vertex t back to a source, target first.  Section 4.4: the
+    // window sequence w_1 ... w_l that gave t its distance, w_l the window of t's final
+    // event; Section 3: the path is a straight segment through the unfolded faces that
+    // sequence crosses, from the pseudo-source to t, then the path to the pseudo-source.
+    // Each segment is walked back along the window chain: the point where it meets a
+    // window's edge, expressed in the parent window's frame (the child edge is the
+    // parent face's edge v0 -> v2 or v2 -> v1), is joined to the parent's pseudo-source
+    // and the line's crossing with the parent's edge is the previous point.
+    // Returns false if the chain is broken (no recorded event, a child not on its
+    // parent's face); an unreachable t gives an empty path.
+    bool trace(int t, std::vector<Pt>& out) const {
+        out.clear();
+        if (!(g[t] < kInf)) return true;
+        int v = t;
+        out.push_back(Pt{0, v, 0.0, 0.0});
+        for (size_t guard = 0; guard <= hist.size() + (size_t)m.nv; ++guard) {
+            const Event& ev = prov[v];
+            if (ev.kind < 0) return g[v] == 0.0;                 // reached a source
+            if (ev.kind == 1) {                                  // along an edge from the fan vertex
+                v = ev.src;
+                out.push_back(Pt{0, v, 0.0, 0.0});
+                continue;
+            }
+            if (ev.kind == 2) {                                  // straight to the face-point source
+                out.push_back(face_point());
+                return true;
+            }
+            const Window* w = &hist[ev.wid];
+            const int h = w->e;
+            const double L = m.len[h];
+            double px, py;
+            pseudo_xy(*w, L, px, py);
+            double x;                                            // where the segment meets w's edge
+            if (v == hfrom(m, h)) {
+                x = 0.0;
+            } else if (v == hto(m, h)) {
+                x = L;
+            } else {                                             // v2: the ray I -> v2 crosses the edge
+                double xc, yc;
+                apex_xy(m, h, xc, yc);
+                x = std::min(std::max(px + (xc - px) * (-py) / (yc - py), 0.0), L);
+                out.push_back(Pt{1, h, x / L, 0.0});
+            }
+            while (w->parent >= 0) {
+                const Window& p = hist[w->parent];
+                const int hp = p.e;
+                const double Lp = m.len[hp];
+                double xc, yc;
+                apex_xy(m, hp, xc, yc);
+                const double f = x / m.len[w->e];
+                double qx, qy;
+                if (w->e == m.twin[prv(hp)]) {                   // left child: edge v0 -> v2
+                    qx = f * xc;
+                    qy = f * yc;
+                } else if (w->e == m.twin[nxt(hp)]) {            // right child: edge v2 -> v1
+                    qx = xc + f * (Lp - xc);
+                    qy = yc - f * yc;
+                } else {
+                    return false;
+                }
+                double ppx, ppy;
+                pseudo_xy(p, Lp, ppx, ppy);
+                x = std::min(std::max(ppx + (qx - ppx) * (-ppy) / (qy - ppy), 0.0), Lp);
+                out.push_back(Pt{1, hp, x / Lp, 0.0});
+                w = &p;
+            }
+            if (w->src < 0) {                                    // an initial window of the face point
+                out.push_back(face_point());
+                return true;
+            }
+            v = w->src;
+            out.push_back(Pt{0, v, 0.0, 0.0});
+        }
+        return false;
     }
 
     int run(const int* targets, int n_targets) {
@@ -436,17 +555,29 @@ struct Solver {
 
 }  // namespace
 
+// Output buffers of oracle_trace_paths.
+struct PathOut {
+    int n_targets;
+    const int* targets;
+    int max_points;
+    int* kinds;
+    int* ids;
+    double* t0;
+    double* t1;
+    int* n_points;
+};
+
 static int solve_field(int nv, const double* xyz, int nf, const int* tri, int src_kind, int src_vertex,
                        int src_face, const double* src_bary, int n_src, const int* srcs, int flags,
                        long long max_windows, int n_targets, const int* targets, double* out,
-                       long long* stats, long long batch_k) {
+                       long long* stats, long long batch_k, const PathOut* paths = nullptr) {
     Mesh m;
     m.nv = nv; m.nf = nf; m.xyz = xyz; m.tri = tri;
     int rc = build_mesh(m);
     if (rc != 0) return rc;
     Solver s(m, flags, max_windows > 0 ? max_windows : (1LL << 40));
     s.batch_k = batch_k > 0 ? batch_k : 1;
-    std::vector<std::pair<int, double>> work;
+    std::vector<Event> work;
     if (src_kind == 0 || src_kind == 2) {
         // Algorithm 1: geod_dist = 0 at the sources; a window on every edge opposite them.
         int count = src_kind == 0 ? 1 : n_src;
@@ -471,10 +602,12 @@ static int solve_field(int nv, const double* xyz, int nf, const int* tri, int sr
             double dx = p[0] - xyz[3 * v], dy = p[1] - xyz[3 * v + 1], dz = p[2] - xyz[3 * v + 2];
             return std::sqrt(dx * dx + dy * dy + dz * dz);
         };
+        s.sface = src_face;
+        for (int k = 0; k < 3; ++k) s.sbary[k] = src_bary[k];
         for (int k = 0; k < 3; ++k) {
             int h = 3 * src_face + k;
             int a = hfrom(m, h), b = hto(m, h);
-            work.push_back({a, dp(a)});
+            work.push_back(Event{a, dp(a), 2, -1, -1});
             int t = m.twin[h];
             if (t >= 0) s.push(Window{0.0, 0.0, m.len[t], dp(b), dp(a), t});
         }
@@ -506,6 +639,25 @@ static int solve_field(int nv, const double* xyz, int nf, const int* tri, int sr
     }
     rc = s.run(targets, n_targets);
     for (int v = 0; v < nv; ++v) out[v] = s.g[v];
+    if (rc == 0 && paths) {
+        std::vector<Solver::Pt> pts;
+        for (int i = 0; i < paths->n_targets; ++i) {
+            const int t = paths->targets[i];
+            if (t < 0 || t >= nv) return -1;
+            if (!s.trace(t, pts)) {
+                paths->n_points[i] = -1;
+                continue;
+            }
+            paths->n_points[i] = (int)pts.size();
+            const size_t base = (size_t)i * paths->max_points;
+            for (size_t j = 0; j < pts.size() && (int)j < paths->max_points; ++j) {
+                paths->kinds[base + j] = pts[j].kind;
+                paths->ids[base + j] = pts[j].id;
+                paths->t0[base + j] = pts[j].t0;
+                paths->t1[base + j] = pts[j].t1;
+            }
+        }
+    }
     if (stats) {
         stats[0] = s.created; stats[1] = s.propagated; stats[2] = s.peak; stats[3] = s.events;
         stats[4] = s.rounds;
@@ -541,6 +693,23 @@ int oracle_cpu_pch(int nv, const double* xyz, int nf, const int* tri, int src_ve
     if (k < 1) return -1;
     return solve_field(nv, xyz, nf, tri, 0, src_vertex, 0, nullptr, 0, nullptr,
                        (flags & ~ORDER_MASK) | ORDER_BATCH, 0, 0, nullptr, out, stats, k);
+}
+
+// Geodesic paths from the source(s) to `targets` (priority-queue order, TRACE on).
+// Source arguments as oracle_geodesic.  For target i, n_points[i] points (target first,
+// the source last; at most max_points stored from i * max_points on) of kinds[]: 0 vertex
+// ids[], 1 point on half-edge ids[] at fraction t0[] from its start, 2 the face-point
+// source in face ids[] with barycentric weights t0[], t1[] of corners 1 and 2;
+// n_points[i] = 0 for an unreachable target, -1 if its window chain was broken.
+// out receives the distance field.  Returns 0, or <0 as oracle_geodesic.
+int oracle_trace_paths(int nv, const double* xyz, int nf, const int* tri, int src_kind, int src_vertex,
+                       int src_face, const double* src_bary, int n_src, const int* srcs, int n_targets,
+                       const int* targets, int max_points, int* kinds, int* ids, double* t0, double* t1,
+                       int* n_points, double* out) {
+    if (n_targets < 0 || max_points < 0) return -1;
+    PathOut po{n_targets, targets, max_points, kinds, ids, t0, t1, n_points};
+    return solve_field(nv, xyz, nf, tri, src_kind, src_vertex, src_face, src_bary, n_src, srcs, ORDER_PQ | TRACE,
+                       0, 0, nullptr, out, nullptr, 1, &po);
 }
 
 // Total angle at every vertex and the pseudo-source flag the oracle uses (for tests).

@@ -27,15 +27,15 @@ MUTATIONS = {
     "no_pseudo_sources": ("m.pseudo[v] = boundary[v] || theta[v] > kTwoPi - 1e-9;", "m.pseudo[v] = 0;"),
     "no_boundary_pseudo_sources": ("m.pseudo[v] = boundary[v] || theta[v] > kTwoPi - 1e-9;",
                                    "m.pseudo[v] = theta[v] > kTwoPi - 1e-9;"),
-    "child_d0_d1_swapped": ("push(Window{w.d, ta, tb, Iv2, w.d1, c})", "push(Window{w.d, ta, tb, w.d1, Iv2, c})"),
+    "child_d0_d1_swapped": ("Window{w.d, ta, tb, Iv2, w.d1, c}", "Window{w.d, ta, tb, w.d1, Iv2, c}"),
     "endpoint_test_wrong_end": ("dominated(w.d + IB, g[v0] + w.B)", "dominated(w.d + IA, g[v0] + w.A)"),
     "occupancy_sign": ("double xs = px + (xc - px) * (-py) / (yc - py);",
                        "double xs = px + (xc - px) * (py) / (yc - py);"),
-    "dropped_v2_event": ("            vertex_event(v2, D2, work);\n", "\n"),
+    "dropped_v2_event": ("            vertex_event(v2, D2, w, work);\n", "\n"),
     "pseudo_source_above_edge": ("    py = -std::sqrt(t > 0 ? t : 0.0);", "    py = std::sqrt(t > 0 ? t : 0.0);"),
     "apex_frame_swapped": ("    xc = ((a - b) * (a + b) + L * L) / (2 * L);", "    xc = ((b - a) * (b + a) + L * L) / (2 * L);"),
     "dominance_without_margin_sign": ("return lhs > rhs * (1.0 + kDomRel);", "return lhs * (1.0 + 1e-3) > rhs;"),
-    "no_fan_at_v0_event": ("if (w.A <= tol) vertex_event(v0, w.d + w.d0, work);", "if (w.A <= tol) {}"),
+    "no_fan_at_v0_event": ("if (w.A <= tol) vertex_event(v0, w.d + w.d0, w, work);", "if (w.A <= tol) {}"),
 }
 
 TINY = [mg.octahedron(0.1, 2, 1), mg.torus(6, 4, seed=6), mg.terrain(5, 4, seed=9, amp_range=(1.0, 3.0)),
