@@ -409,6 +409,66 @@ def run_workload(args):
         h.close()
 
 
+def run_paths(args):
+    """Report line for geodesic paths on the benchmark terrain (512 x 512 quads, source at
+    the centre): the solve with distance events recorded against the plain solve (same
+    tuned configuration), and the paths of 4,096 seeded target vertices traced on the
+    device.  Times: the solves' device time (CUDA events inside the library) and the wall
+    time of the whole pch_trace_paths call (target upload, solve, event pick, trace,
+    download of the points).  Check: the 3D length of every traced path against the
+    target's distance (a property of an exact geodesic at any size)."""
+    import time
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1293_gb300 import meshgen as mg, pch
+    meshes, srcs = mg.workload("terrain", "full")
+    m, src = meshes[0], int(srcs[0][0])
+    h = pch.Mesh(m.vertices, m.faces)
+    tuned = pch.autotune(h, src, cache_path=os.path.join(ROOT, "paper_1305_1293_gb300", "autotune_cache.txt"))
+    tk = {"k": tuned["k"], "block": tuned["block"], "hops": tuned["hops"]}
+    rng = np.random.default_rng(0xC0FFEE + 1)
+    targets = rng.choice(m.nv, size=4096, replace=False).astype(np.int32)
+    pch.solve(h, src, **tk)                                           # warm the graph
+    _, st_plain = pch.solve(h, src, stats=True, **tk)
+    pch.trace_paths(h, [src], targets[:8], max_points=4096, **tk)     # warm the recording graph
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    d, paths, st = pch.trace_paths(h, [src], targets, max_points=4096, stats=True, **tk)
+    wall_ms = (time.perf_counter() - t0) * 1e3
+    failed = sum(p is None for p in paths)
+    npts, worst = [], 0.0
+    for t, p in zip(targets, paths):
+        if p is None:
+            continue
+        kind, pid, a, b = p
+        xyz = np.empty((len(kind), 3))
+        for j in range(len(kind)):
+            if kind[j] == 0:
+                xyz[j] = m.vertices[pid[j]]
+            elif kind[j] == 1:
+                f, i = divmod(int(pid[j]), 3)
+                u, w = m.vertices[m.faces[f, i]], m.vertices[m.faces[f, (i + 1) % 3]]
+                xyz[j] = u + a[j] * (w - u)
+            else:
+                c = m.faces[int(pid[j])]
+                xyz[j] = (1 - a[j] - b[j]) * m.vertices[c[0]] + a[j] * m.vertices[c[1]] + b[j] * m.vertices[c[2]]
+        length = float(np.linalg.norm(np.diff(xyz, axis=0), axis=1).sum())
+        if d[t] > 0:
+            worst = max(worst, abs(length - d[t]) / d[t])
+        npts.append(len(kind))
+    line = {"workload": "paths", "mesh": "terrain 512x512 (524,288 faces), centre source",
+            "targets": int(len(targets)), "failed_traces": int(failed),
+            "mean_points_per_path": float(np.mean(npts)), "max_points_per_path": int(np.max(npts)),
+            "plain_solve_ms": st_plain["ms_total"], "recording_solve_ms": st["ms_total"],
+            "recording_overhead": st["ms_total"] / st_plain["ms_total"],
+            "trace_call_wall_ms": wall_ms, "paths_per_s_wall": len(targets) / (wall_ms / 1e3),
+            "length_vs_distance_max_rel_err": worst, "tuned": tk}
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -418,13 +478,15 @@ def main():
     ap.add_argument("--k", type=int, default=0, help="windows per iteration (0 = autotuned)")
     ap.add_argument("--hops", type=int, default=0, help="with --k: propagation hops (0 = library default)")
     ap.add_argument("--workload", default="terrain",
-                    choices=["terrain", "icosphere", "torus", "batch", "multisrc", "large"],
+                    choices=["terrain", "icosphere", "torus", "batch", "multisrc", "large", "paths"],
                     help="terrain = the benchmark line; others print a per-workload report line")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="iteration driver: CUDA graph with device-side termination, or host-driven (for ncu)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "paths":
+        run_paths(args)
     elif args.workload != "terrain":
         run_workload(args)
     else:

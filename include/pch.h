@@ -161,6 +161,48 @@ pch_status pch_solve_multi(pch_mesh* m, const pch_source* srcs, int32_t n_source
 pch_status pch_solve_batch(pch_mesh* const* meshes, const pch_source* srcs, int32_t n_instances,
                            const pch_options* opt, double* const* out_dists, pch_stats* stats);
 
+/* ---- geodesic paths (Section 4.4, Section 3) ---------------------------------------- */
+enum {
+    PCH_POINT_VERTEX = 0,     /* mesh vertex `id` */
+    PCH_POINT_EDGE = 1,       /* on half-edge `id` (3 f + i runs from corner i to corner (i + 1) % 3
+                                 of face f) at fraction t0 of its length from its start; the
+                                 path crosses the edge into (or out of) face f */
+    PCH_POINT_FACE = 2        /* the face-point source inside face `id`: barycentric weights t0,
+                                 t1 of corners 1 and 2 (corner 0 has 1 - t0 - t1) */
+};
+
+/* A point of a geodesic path on the surface. */
+typedef struct {
+    int32_t kind;             /* PCH_POINT_* */
+    int32_t id;
+    double t0, t1;
+} pch_path_point;
+
+/* Exact geodesic paths from the source(s) to the vertices targets[0 .. n_targets-1].
+ * Solves the field as pch_solve_multi does while recording every distance event that
+ * lowered a vertex's distance, with its window (edge, pseudo-source position, pseudo-
+ * source vertex).  The event whose distance is the vertex's final one comes from the
+ * last window of the window sequence that carries its shortest path (Section 4.4).  A
+ * device kernel then walks each path back from its target: a straight segment through
+ * the faces unfolded along that window's strip to the window's pseudo-source (Section 3:
+ * a geodesic is straight in every unfolding and bends only at saddle or boundary
+ * vertices), then on from that vertex's own event, until a source.
+ * points (host): n_targets x max_points entries; path i starts at points[i * max_points],
+ * target first, source (or the face-point source) last, with every edge crossing and
+ * every vertex it passes.  Consecutive points may coincide where the recorded window
+ * chain touches a vertex (an edge point at an end of its edge, next to that vertex):
+ * zero-length steps of the same path.  n_points (host, n_targets entries): the path's point count;
+ * when it exceeds max_points only its first max_points points are stored; 0 for an
+ * unreachable target; -1 if a trace failed numerically (it left the mesh, met a vertex
+ * without a recorded event, found no edge to cross where a path passes exactly through a
+ * vertex that is not its pseudo-source, or exceeded 2^22 steps).  out_dist (host, n_vertices) may be
+ * NULL.  opt is used as by pch_solve_multi except that out_on_device is ignored (all
+ * outputs are host arrays).  Errors: as pch_solve_multi, and INVALID_ARG for a target
+ * out of range or max_points < 1. */
+pch_status pch_trace_paths(pch_mesh* m, const pch_source* srcs, int32_t n_sources, const pch_options* opt,
+                           const int32_t* targets, int32_t n_targets, int32_t max_points,
+                           pch_path_point* points, int32_t* n_points, double* out_dist, pch_stats* stats);
+
 /* Release a mesh and its workspace (NULL is a no-op). */
 void pch_destroy(pch_mesh* m);
 

@@ -137,7 +137,7 @@ struct Counters {
     unsigned long long examined, occupied, children, rays;   // propagation path counts (FP64 op tally)
     unsigned long long scanned, sorted;               // windows read by compaction / sorted
     int work_next;          // next work-list index handed to a propagation lane
-    int pad2;
+    int n_plog;             // provenance records written (geodesic paths)
 };
 
 enum : int {
@@ -145,7 +145,22 @@ enum : int {
     kErrReqFull = 2,
     kErrIter = 4,
     kErrNaN = 8,
+    kErrProvFull = 16,
 };
+
+// Provenance of a distance event that lowered a vertex's distance (geodesic paths).  The
+// record whose distance equals the vertex's final one comes from the last window of the
+// window sequence that carries the vertex's shortest path (Section 4.4).
+struct ProvRec {
+    unsigned long long db;   // the event's distance (ordered bit image)
+    int inst, v;             // instance, vertex
+    int h;                   // kind 0: the window's half-edge; kind 2: a half-edge of the source's face
+    int src;                 // pseudo-source vertex (-1: the face-point source)
+    int kind;                // 0 window event, 1 along a boundary edge from src, 2 corner of the source's face
+    int pad;
+    double px, py;           // kind 0: pseudo-source, kind 2: the face point, in h's frame
+};
+static_assert(sizeof(ProvRec) == 48, "ProvRec layout");
 
 // A pseudo-source fan candidate: a distance event at a saddle or boundary vertex, with
 // the direction it arrived from.
@@ -183,6 +198,9 @@ struct Work {
     int stride_T;
     unsigned long long* sthr_key;
     int* sthr_idx;
+    // geodesic paths: distance events that lowered a vertex's distance (nullptr: off)
+    ProvRec* plog;
+    int plog_cap;
 };
 
 // Ordered u64 image of a nonnegative double (atomicMin-able, Section 4.2 Step 4).

@@ -85,15 +85,40 @@ __device__ __forceinline__ void warp_add_ull(unsigned long long* c, int x) {
     if ((threadIdx.x & 31) == 0 && t) atomicAdd(c, (unsigned long long)t);
 }
 
+// Where a distance event came from (kept only for geodesic paths): the window's half-edge
+// h, its pseudo-source vertex src and position (px, py) in h's frame (kind 0); a fan's
+// event along a boundary edge from src (kind 1); a corner of the face-point source's face
+// with the point at (px, py) in h's frame (kind 2).
+struct EvSrc {
+    int inst, h, src, kind;
+    double px, py;
+};
+
+__device__ __forceinline__ void log_event(const Work& w, const EvSrc& es, unsigned v, unsigned long long db) {
+    const int slot = atomicAdd(&w.cnt->n_plog, 1);
+    if (slot < w.plog_cap) {
+        ProvRec r;
+        r.db = db; r.inst = es.inst; r.v = (int)v; r.h = es.h; r.src = es.src; r.kind = es.kind; r.pad = 0;
+        r.px = es.px; r.py = es.py;
+        w.plog[slot] = r;
+    } else {
+        atomicOr(&w.cnt->error, kErrProvFull);
+    }
+}
+
 // Distance event (Algorithm 2, Algorithm 4): min into geod_dist.  Returns true when the
 // event lowered the distance of a pseudo-source vertex: the caller then files a fan
-// candidate carrying the event's incoming direction.
-__device__ __forceinline__ bool vertex_event(const Inst& I, unsigned vf, double D, double& gcache) {
+// candidate carrying the event's incoming direction.  With PROV an event that lowered the
+// distance is also recorded with its origin `es` (geodesic paths).
+template <bool PROV = false>
+__device__ __forceinline__ bool vertex_event(const Inst& I, unsigned vf, double D, double& gcache,
+                                             const Work* w = nullptr, const EvSrc* es = nullptr) {
     if (!lt_s(D, gcache)) return false;
     unsigned v = vf & ~kPseudoBit;
     unsigned long long nb = dbits(D);
     unsigned long long old = atomicMin(I.g + v, nb);
     if (nb < old) {
+        if constexpr (PROV) log_event(*w, *es, v, nb);
         gcache = D;
         return (vf & kPseudoBit) != 0;
     }
@@ -224,7 +249,8 @@ __global__ void k_init_face_sources(Work w, const SrcDev* __restrict__ srcs, int
             double x = b1 * R.L + b2 * R.xc, y = b2 * R.yc;        // point in h's frame
             double dstart = sqrt(x * x + y * y);
             double gc = ldg_dist(I.g, R.v0 & ~kPseudoBit);
-            if (vertex_event(I, R.v0, dstart, gc)) {
+            const EvSrc es{s.inst, h, -1, 2, x, y};
+            if (w.plog ? vertex_event<true>(I, R.v0, dstart, gc, &w, &es) : vertex_event(I, R.v0, dstart, gc)) {
                 // incoming direction: from the corner towards the point, inside face(h)
                 push_fan(w.req[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, R.v0 & ~kPseudoBit, dstart, h, x, y);
             }
@@ -458,6 +484,7 @@ constexpr int kHopTask = 1 << 30;   // hop-field flag of a queue entry: a deferr
 // both children exist the left one is deferred to q as a task (if q has room).  A task
 // (task = true) skips the window's own part, done in an earlier round, and computes the
 // left child only; IB_in then holds |I v2|.
+template <bool PROV>
 __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, FanReq* req, int inst,
                                                  int src, double d, int h, double A, double B, double px, double py,
                                                  bool task, int hop, const TaskQueue& q, ChildOut& c0, ChildOut& c1,
@@ -493,19 +520,20 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
             // ago; distances only fall, so repeating them could only prune more, never keep
             // a window that must go, and they are skipped.
             prop = true;
+            const EvSrc es{inst, h, src, 0, px, py};   // event origin, recorded with PROV only
             const double py2 = py * py;
             const double tol = times_eps(L);
             const double tiny = tol;
             // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
             if (le_s(A, tol)) {
                 double D0 = d + (sbits(A) == 0 ? IA : sqrt_nr(fma(px, px, py2)));
-                if (vertex_event(I, R.v0, D0, g0))   // the ray arrives at v0 from I (h's frame)
+                if (vertex_event<PROV>(I, R.v0, D0, g0, &w, &es))   // the ray arrives at v0 from I (h's frame)
                     push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v0 & ~kPseudoBit, D0, h, px, py);
             }
             if (sbits(L) - sbits(B) <= kSnapUlps) {
                 double q = L - px;
                 double D1 = d + (sbits(B) == sbits(L) ? IB : sqrt_nr(fma(q, q, py2)));
-                if (vertex_event(I, R.v1, D1, g1))   // at v1, in the frame of twin(h) = (v1 -> v0)
+                if (vertex_event<PROV>(I, R.v1, D1, g1, &w, &es))   // at v1, in the frame of twin(h) = (v1 -> v0)
                     push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v1 & ~kPseudoBit, D1, R.twin, q, -py);
             }
             // occupancy of v2: the ray I -> v2 crosses e at xs = px + num / den;
@@ -540,7 +568,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                     right = angle_pos(xq - kSplitTol) > q;
                     if (!left && !right) left = right = true;
                 }
-                if (vertex_event(I, R.v2, D2, g2)) {
+                if (vertex_event<PROV>(I, R.v2, D2, g2, &w, &es)) {
                     // the ray arrives at v2 inside face(h); direction to I in the frame of
                     // prev(h) = (v2 -> v0), whose axis is (-xc, -yc) / L2
                     const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
@@ -641,6 +669,8 @@ constexpr int kPropQueueBytesPerThread = 2 * (7 * 8 + 4 * 4);
 // Repacking the chains onto the lowest lanes every round keeps the warps that do issue
 // FP64 work full once the selected list runs dry, and leaves the other warps idle.
 // 168 registers a thread at most (148 used, no spills): 6 blocks of 64 threads per SM.
+// PROV: also record the distance events (geodesic paths).
+template <bool PROV>
 __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
     extern __shared__ double q_mem[];   // blockDim.x * kPropQueueBytesPerThread bytes
     const int QB = 2 * blockDim.x;
@@ -731,8 +761,8 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
         const TaskQueue tq{q_d + wo, q_A + wo, q_B + wo, q_px + wo, q_py + wo, q_IA + wo, q_IB + wo,
                            q_he + wo, q_inst + wo, q_src + wo, q_hop + wo, &s_nq[(r + 1) % 3], (int)blockDim.x};
         if (have)
-            prop = propagate_window(w, cnt, req, inst, src, d, h, A, B, px, py, task, hop, tq, c0, c1, nch, occ,
-                                    ncomp, nray, cIA, cIB);
+            prop = propagate_window<PROV>(w, cnt, req, inst, src, d, h, A, B, px, py, task, hop, tq, c0, c1, nch,
+                                          occ, ncomp, nray, cIA, cIB);
         bool cont = have && nch > 0 && hop + 1 < hops && le_s(c0.key, w.ctl[inst].tau) &&
                     (!dry || nq >= tail_cut) && seen_child < room;
         // the continuing child goes to the queue while it has room, every other child to
@@ -807,7 +837,8 @@ __device__ __forceinline__ double fan_hit(const HERec& Ro, double2 z) {
 }
 
 // kFanLanes lanes per fan candidate; lane j of the group handles corners j, j + 8, ...
-// of the vertex's one-ring.
+// of the vertex's one-ring.  PROV: also record the distance events (geodesic paths).
+template <bool PROV>
 __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
     Counters* cnt = w.cnt;
     if (cnt->halt) return;
@@ -937,10 +968,11 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                 // boundary edge: endpoint events for the covered endpoints
                 const unsigned a = Ro.v0 & ~kPseudoBit, b = Ro.v1 & ~kPseudoBit;
                 double ga = ldg_dist(I.g, a), gb = ldg_dist(I.g, b);
+                const EvSrc es{rq.inst, o, (int)v, 1, 0.0, 0.0};   // along the edge from v (PROV only)
                 // incoming directions: at a towards v, in o's frame; at b along next(o) = (b -> v)
-                if (s0 <= 0.0 && vertex_event(I, Ro.v0, D + Ro.L2, ga))
+                if (s0 <= 0.0 && vertex_event<PROV>(I, Ro.v0, D + Ro.L2, ga, &w, &es))
                     push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, a, D + Ro.L2, o, Ro.xc, Ro.yc);
-                if (s1 >= Lo && vertex_event(I, Ro.v1, D + Ro.L1, gb))
+                if (s1 >= Lo && vertex_event<PROV>(I, Ro.v1, D + Ro.L1, gb, &w, &es))
                     push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, b, D + Ro.L1, he_next(o), 1.0,
                              0.0);
                 continue;
@@ -1098,6 +1130,9 @@ struct Workspace {
     Alloc fixed;            // counters, tables
     Alloc sthr;             // strided-selection thresholds (PCH_CONTROL_STRIDED)
     int sthr_cap = 0;
+    Alloc plog_mem;         // distance-event records (geodesic paths)
+    int plog_cap = 0;
+    ProvRec* plog = nullptr;
     Work w{};
     int pool_cap = 0, sel_cap = 0, arena_cap = 0, req_cap = 0;
     long long g_cap = 0, ang_cap = 0, st_cap = 0;
@@ -1125,6 +1160,7 @@ void destroy_workspace(Workspace* ws) {
     ws->inst_mem.release();
     ws->fixed.release();
     ws->sthr.release();
+    ws->plog_mem.release();
     if (ws->cnt_host) cudaFreeHost(ws->cnt_host);
     for (auto& e : ws->ev) if (e) cudaEventDestroy(e);
     delete ws;
@@ -1300,10 +1336,13 @@ static cudaError_t launch_iteration(Workspace* ws, cudaStream_t s, const SolveCf
     }
     k_compact<<<grid_for(4), tpb, 0, s>>>(w);
     if (ev) cudaEventRecord(ev[1], s);
-    k_propagate<<<grid_for(cfg.prop_blocks_per_sm), cfg.prop_threads, cfg.prop_threads * kPropQueueBytesPerThread, s>>>(
-        w, cfg.hops, cfg.tail_cut);
+    const dim3 pg(grid_for(cfg.prop_blocks_per_sm));
+    const size_t psh = (size_t)cfg.prop_threads * kPropQueueBytesPerThread;
+    if (cfg.prov) k_propagate<true><<<pg, cfg.prop_threads, psh, s>>>(w, cfg.hops, cfg.tail_cut);
+    else k_propagate<false><<<pg, cfg.prop_threads, psh, s>>>(w, cfg.hops, cfg.tail_cut);
     if (ev) cudaEventRecord(ev[2], s);
-    k_fan<<<grid_for(2), 256, 0, s>>>(w, cfg.full_fan);
+    if (cfg.prov) k_fan<true><<<grid_for(2), 256, 0, s>>>(w, cfg.full_fan);
+    else k_fan<false><<<grid_for(2), 256, 0, s>>>(w, cfg.full_fan);
     if (ev) cudaEventRecord(ev[3], s);
     unsigned* kb[2] = {w.sort_key[0], w.sort_key[1]};
     int* vb[2] = {w.sort_val[0], w.sort_val[1]};
@@ -1358,6 +1397,7 @@ static pch_status build_graph(Workspace* ws, cudaStream_t s, const SolveCfg& cfg
 static pch_status status_from_error(int err) {
     if (err & kErrIter) return set_error(PCH_ERR_TIMEOUT, "iteration cap reached before all windows were processed");
     if (err & (kErrPoolFull | kErrReqFull)) return set_error(PCH_ERR_CAPACITY, "window pool capacity exceeded (error %d)", err);
+    if (err & kErrProvFull) return set_error(PCH_ERR_CAPACITY, "distance-event record capacity exceeded");
     return set_error(PCH_ERR_CUDA, "solver error flags %d", err);
 }
 
@@ -1490,6 +1530,7 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     cfg.key_bits = bits;
     cfg.mlp = nullptr;
     cfg.stride_T = cfg.stride_m = 0;
+    cfg.prov = 0;
     if (cfg.control == PCH_CONTROL_STRIDED) {
         // Section 5.1: T threads each select their ceil(k / T) nearest windows.  T is the
         // number of threads the GPU holds at once (2048 per SM); each selects M of them, M
@@ -1508,8 +1549,25 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
 }
 
 // Solve a set of instances.  srcs[i].inst says which instance a source seeds.
+// Grow the distance-event records to hold `cap` (geodesic paths).
+static pch_status ensure_plog(Workspace* ws, long long cap) {
+    cap = std::min<long long>(cap, 1LL << 30);
+    if (cap <= ws->plog_cap) return PCH_OK;
+    drop_graph(ws);
+    ws->plog_mem.release();
+    ws->plog_cap = 0;
+    ws->plog = nullptr;
+    if (ws->plog_mem.get(&ws->plog, (size_t)cap) != cudaSuccess) {
+        ws->plog_mem.release();
+        ws->plog = nullptr;
+        return set_error(PCH_ERR_OOM, "distance-event records: allocation of %lld failed", cap);
+    }
+    ws->plog_cap = (int)cap;
+    return PCH_OK;
+}
+
 pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* srcs, int n_src, const pch_options* opt,
-                           double* const* outs, int out_mode, pch_stats* stats) {
+                           double* const* outs, int out_mode, pch_stats* stats, int prov) {
     clear_error();
     if (!meshes || n_inst <= 0 || !srcs || n_src <= 0) return set_error(PCH_ERR_INVALID_ARG, "empty solve");
     for (int i = 0; i < n_inst; ++i)
@@ -1595,6 +1653,11 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
         ws->sthr_cap = cfg.stride_T;
     }
     w.stride_T = cfg.stride_T;
+    cfg.prov = prov ? 1 : 0;
+    if (prov) {
+        st = ensure_plog(ws, std::max<long long>(1 << 20, 4 * goff));
+        if (st != PCH_OK) return st;
+    }
     ws->trace_on = opt && (opt->flags & PCH_FLAG_TRACE);
     if (ws->trace_on && !ws->trace_buf) {
         ws->trace_cap = 1 << 18;
@@ -1607,8 +1670,11 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
     w.trace_rows = ws->trace_rows;
     if (cfg.control == PCH_CONTROL_LEARNED) cfg.mlp = mlp_device_params();
     // a fan-request overflow fails the attempt (a lost request would lose a fan); the
-    // solve is then run again from the start with twice the request room
+    // solve is then run again from the start with twice the request room (the same for
+    // the distance-event records of a geodesic-path solve)
     for (int attempt = 0;; ++attempt) {
+        w.plog = prov ? ws->plog : nullptr;
+        w.plog_cap = prov ? ws->plog_cap : 0;
         // upload tables, clear state
         PCH_CUDA(cudaMemcpyAsync(w.inst, hinst.data(), sizeof(Inst) * n_inst, cudaMemcpyHostToDevice, s));
         PCH_CUDA(cudaMemcpyAsync(w.ctl, hctl.data(), sizeof(InstCtl) * n_inst, cudaMemcpyHostToDevice, s));
@@ -1635,6 +1701,12 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
             clear_error();
             continue;
         }
+        if (st == PCH_ERR_CAPACITY && (ws->cnt_host->error & kErrProvFull) && attempt < 4) {
+            st = ensure_plog(ws, std::max<long long>(2LL * ws->plog_cap, (long long)ws->cnt_host->n_plog + 1));
+            if (st != PCH_OK) return st;
+            clear_error();
+            continue;
+        }
         if (st != PCH_OK) return st;
         break;
     }
@@ -1651,6 +1723,215 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
     }
     PCH_CUDA(cudaGetLastError());
     if (out_mode != kOutDevice) PCH_CUDA(cudaStreamSynchronize(s));
+    return PCH_OK;
+}
+
+// ====================================================================== geodesic paths
+// Section 4.4: the window that finally assigns a vertex its distance is the last of a
+// window sequence carrying its shortest path; Section 3: that path is a straight segment
+// in the unfolding of the faces the sequence crosses, from the window's pseudo-source,
+// and from there the pseudo-source's own path.
+
+constexpr int kNoPick = 0x7f7f7f7f;          // per-vertex pick before any record matched
+constexpr long long kTraceMaxSteps = 1 << 22;
+
+// Per vertex of instance 0: the first record whose distance is the vertex's final one.
+__global__ void k_prov_pick(const ProvRec* __restrict__ log, int n, const unsigned long long* __restrict__ g, int nv,
+                            int* pick) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const ProvRec r = log[i];
+        if (r.inst == 0 && r.v >= 0 && r.v < nv && r.db == g[r.v]) atomicMin(pick + r.v, i);
+    }
+}
+
+// Barycentric weights over the stored corners of face(e) of the point (x, y) in e's frame.
+__device__ __forceinline__ pch_path_point face_point(const HERec& E, int e, double x, double y) {
+    const double b2 = y / E.yc, b1 = (x - b2 * E.xc) / E.L, b0 = 1.0 - b1 - b2;
+    double b[3];
+    const int i = e % 3;
+    b[i] = b0;
+    b[(i + 1) % 3] = b1;
+    b[(i + 2) % 3] = b2;
+    pch_path_point p;
+    p.kind = PCH_POINT_FACE; p.id = e / 3; p.t0 = b[1]; p.t1 = b[2];
+    return p;
+}
+
+// One thread per target.  A segment from vertex v back to its window's pseudo-source I
+// (coordinates in the window's edge frame h) leaves v's position in that frame; it
+// crosses h (unless v is an end of h) into twin(h)'s face.  In a face entered through
+// half-edge e (the point P on e's axis, I beyond e's apex side, y > 0) the segment ends
+// at the apex when that is the pseudo-source; else it leaves through edge v1 -> v2 or
+// v2 -> v0, on the side of the line P -> apex where I lies, and P, I are carried into
+// the frame of that edge's twin, the next face.  A crossing is reported on the edge of
+// the face the path has just traversed (the side of the target), like a window's edge.
+__global__ void k_trace(Inst In, const ProvRec* __restrict__ log, const int* __restrict__ pick,
+                        const int* __restrict__ targets, int n_targets, int max_points, pch_path_point* out,
+                        int* n_out) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_targets; i += gridDim.x * blockDim.x) {
+        pch_path_point* po = out + (size_t)i * max_points;
+        int np = 0;
+        auto emit = [&](const pch_path_point& p) {
+            if (np < max_points) po[np] = p;
+            ++np;
+        };
+        auto vertex_pt = [](int v) {
+            pch_path_point p;
+            p.kind = PCH_POINT_VERTEX; p.id = v; p.t0 = 0.0; p.t1 = 0.0;
+            return p;
+        };
+        auto edge_pt = [](int h, double t) {
+            pch_path_point p;
+            p.kind = PCH_POINT_EDGE; p.id = h; p.t0 = t; p.t1 = 0.0;
+            return p;
+        };
+        int v = targets[i];
+        if (In.g[v] >= 0x7FF0000000000000ull) {   // +inf: unreachable, no path
+            n_out[i] = 0;
+            continue;
+        }
+        emit(vertex_pt(v));
+        bool ok = false;
+        long long steps = 0;
+        while (steps++ < kTraceMaxSteps) {
+            if (In.g[v] == 0ull) {              // a source
+                ok = true;
+                break;
+            }
+            const int pi = pick[v];
+            if (pi == kNoPick) break;
+            const ProvRec r = log[pi];
+            if (r.kind == 1) {                   // along a boundary edge from the fan vertex
+                if (r.src < 0 || r.src >= In.nv) break;
+                v = r.src;
+                emit(vertex_pt(v));
+                continue;
+            }
+            if (r.h < 0 || r.h >= In.nh) break;
+            const HERec R = In.rec[r.h];
+            if (r.kind == 2) {                   // straight to the face-point source
+                emit(face_point(R, r.h, r.px, r.py));
+                ok = true;
+                break;
+            }
+            // kind 0: v is an end or the apex of the window's edge h
+            const double L = R.L;
+            double x;
+            if (v == (int)(R.v0 & ~kPseudoBit)) {
+                x = 0.0;
+            } else if (v == (int)(R.v1 & ~kPseudoBit)) {
+                x = L;
+            } else if (v == (int)(R.v2 & ~kPseudoBit)) {
+                x = r.px + (R.xc - r.px) * (-r.py) / (R.yc - r.py);
+                x = x < 0.0 ? 0.0 : (x > L ? L : x);
+                emit(edge_pt(r.h, x / L));
+            } else {
+                break;
+            }
+            int e = R.twin;
+            double Px = L - x, Ix = L - r.px, Iy = -r.py;
+            const double seg = sqrt((Ix - Px) * (Ix - Px) + Iy * Iy);
+            bool seg_done = false, path_done = false;
+            while (e >= 0 && e < In.nh && steps++ < kTraceMaxSteps) {
+                const HERec E = In.rec[e];
+                const int a2 = (int)(E.v2 & ~kPseudoBit);
+                const double tol = 1e-7 * (E.L + seg);
+                if (r.src >= 0 && r.src == a2 && (Ix - E.xc) * (Ix - E.xc) + (Iy - E.yc) * (Iy - E.yc) <= tol * tol) {
+                    v = a2;                      // reached the pseudo-source
+                    emit(vertex_pt(v));
+                    seg_done = true;
+                    break;
+                }
+                if (r.src < 0) {                 // the face-point source inside this face?
+                    const double b2 = Iy / E.yc, b1 = (Ix - b2 * E.xc) / E.L;
+                    if (b2 >= -1e-9 && b1 >= -1e-9 && 1.0 - b1 - b2 >= -1e-9) {
+                        emit(face_point(E, e, Ix, Iy));
+                        path_done = true;
+                        break;
+                    }
+                }
+                // leave through v1 -> v2 (I right of P -> apex) or v2 -> v0; if the crossing
+                // falls outside that edge (a near-vertex pass) take the other one
+                const bool right0 = (E.xc - Px) * Iy - E.yc * (Ix - Px) < 0.0;
+                bool crossed = false;
+                for (int attempt = 0; attempt < 2 && !crossed; ++attempt) {
+                    const bool right = attempt == 0 ? right0 : !right0;
+                    const int f = right ? E.tw1 : E.tw2;
+                    if (f < 0) continue;
+                    const double Lf = right ? E.L1 : E.L2;
+                    const double ox = right ? E.xc : 0.0, oy = right ? E.yc : 0.0;
+                    const double ux = (right ? E.L - E.xc : E.xc) / Lf, uy = (right ? -E.yc : E.yc) / Lf;
+                    const double prx = Px - ox, pry = -oy, irx = Ix - ox, iry = Iy - oy;
+                    const double pfx = prx * ux + pry * uy, pfy = ux * pry - uy * prx;
+                    const double ifx = irx * ux + iry * uy, ify = ux * iry - uy * irx;
+                    const double den = ify - pfy;
+                    if (!(den > 0.0)) continue;
+                    double xf = pfx + (ifx - pfx) * (-pfy) / den;
+                    const double slack = 1e-9 * Lf;
+                    if (!(xf >= -slack && xf <= Lf + slack)) continue;
+                    xf = xf < 0.0 ? 0.0 : (xf > Lf ? Lf : xf);
+                    const int exit_he = right ? he_next(e) : 3 * (e / 3) + (e % 3 + 2) % 3;
+                    emit(edge_pt(exit_he, 1.0 - xf / Lf));
+                    e = f;
+                    Px = xf;
+                    Ix = ifx;
+                    Iy = ify;
+                    crossed = true;
+                }
+                if (!crossed) break;
+            }
+            if (path_done) {
+                ok = true;
+                break;
+            }
+            if (!seg_done) break;
+        }
+        n_out[i] = ok ? np : -1;
+    }
+}
+
+// Solve with the distance events recorded, then trace every target's path.
+static pch_status trace_paths(pch_mesh* m, const SrcDev* sd, int n_src, const pch_options* opt, const int* targets,
+                              int n_targets, int max_points, pch_path_point* points, int* n_points, double* out_dist,
+                              pch_stats* stats) {
+    pch_options o = opt ? *opt : pch_options{};
+    o.out_on_device = 0;
+    double* outs[1] = {out_dist};
+    pch_status st = solve_instances(&m, 1, sd, n_src, &o, outs, out_dist ? kOutHost : kOutNone, stats, 1);
+    if (st != PCH_OK) return st;
+    Workspace* ws = m->ws;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    const int nv = m->dm.nv;
+    const int n_rec = std::min(ws->cnt_host->n_plog, ws->plog_cap);
+    Inst I{};
+    PCH_CUDA(cudaMemcpyAsync(&I, ws->w.inst, sizeof(Inst), cudaMemcpyDeviceToHost, s));
+    int *dpick = nullptr, *dtg = nullptr, *dn = nullptr;
+    pch_path_point* dpts = nullptr;
+    const size_t npts = (size_t)std::max(n_targets, 1) * (size_t)max_points;
+    cudaError_t e = cudaMallocAsync(&dpick, sizeof(int) * (size_t)nv, s);
+    if (!e) e = cudaMallocAsync(&dtg, sizeof(int) * (size_t)std::max(n_targets, 1), s);
+    if (!e) e = cudaMallocAsync(&dn, sizeof(int) * (size_t)std::max(n_targets, 1), s);
+    if (!e) e = cudaMallocAsync(&dpts, sizeof(pch_path_point) * npts, s);
+    if (!e && n_targets > 0) e = cudaMemcpyAsync(dtg, targets, sizeof(int) * (size_t)n_targets, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemsetAsync(dpick, 0x7f, sizeof(int) * (size_t)nv, s);
+    if (!e) e = cudaStreamSynchronize(s);   // I (the instance table) is needed by value
+    if (!e) {
+        k_prov_pick<<<grid_for(4), 256, 0, s>>>(ws->plog, n_rec, I.g, nv, dpick);
+        if (n_targets > 0)
+            k_trace<<<(n_targets + 127) / 128, 128, 0, s>>>(I, ws->plog, dpick, dtg, n_targets, max_points, dpts, dn);
+        e = cudaGetLastError();
+    }
+    if (!e && n_targets > 0) e = cudaMemcpyAsync(n_points, dn, sizeof(int) * (size_t)n_targets, cudaMemcpyDeviceToHost, s);
+    if (!e && n_targets > 0)
+        e = cudaMemcpyAsync(points, dpts, sizeof(pch_path_point) * (size_t)n_targets * max_points, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(dpick, s);
+    cudaFreeAsync(dtg, s);
+    cudaFreeAsync(dn, s);
+    cudaFreeAsync(dpts, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return set_error(e == cudaErrorMemoryAllocation ? PCH_ERR_OOM : PCH_ERR_CUDA, "path trace: %s",
+                            cudaGetErrorString(e));
+    if (stats) stats->kernel_launches += n_targets > 0 ? 2 : 1;
     return PCH_OK;
 }
 
@@ -1694,6 +1975,26 @@ extern "C" pch_status pch_solve_batch(pch_mesh* const* meshes, const pch_source*
     }
     return solve_instances(meshes, n_instances, sd.data(), n_instances, opt, out_dists,
                            (opt && opt->out_on_device) ? kOutDevice : kOutHost, stats);
+}
+
+extern "C" pch_status pch_trace_paths(pch_mesh* m, const pch_source* srcs, int32_t n_sources, const pch_options* opt,
+                                      const int32_t* targets, int32_t n_targets, int32_t max_points,
+                                      pch_path_point* points, int32_t* n_points, double* out_dist, pch_stats* stats) {
+    clear_error();
+    if (!m || !srcs || n_sources <= 0 || n_targets < 0 || max_points < 1)
+        return set_error(PCH_ERR_INVALID_ARG, "null argument, no source, n_targets < 0 or max_points < 1");
+    if (n_targets > 0 && (!targets || !points || !n_points)) return set_error(PCH_ERR_INVALID_ARG, "null path buffers");
+    if ((long long)n_targets * (long long)max_points > (1LL << 31))
+        return set_error(PCH_ERR_CAPACITY, "n_targets * max_points exceeds 2^31 points");
+    for (int i = 0; i < n_targets; ++i)
+        if (targets[i] < 0 || targets[i] >= m->dm.nv) return set_error(PCH_ERR_INVALID_ARG, "target %d out of range", targets[i]);
+    std::vector<SrcDev> sd(n_sources);
+    for (int i = 0; i < n_sources; ++i) {
+        sd[i] = SrcDev{};
+        sd[i].inst = 0; sd[i].kind = srcs[i].kind; sd[i].vertex = srcs[i].vertex; sd[i].face = srcs[i].face;
+        for (int k = 0; k < 3; ++k) sd[i].bary[k] = srcs[i].bary[k];
+    }
+    return trace_paths(m, sd.data(), n_sources, opt, targets, n_targets, max_points, points, n_points, out_dist, stats);
 }
 
 extern "C" pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float* chosen, int32_t* n_rows) {

@@ -26,6 +26,7 @@ struct SolveCfg {
     int tail_cut;           // stop chaining once the selected list is dry and fewer entries are queued
     int stride_T;           // PCH_CONTROL_STRIDED: virtual threads of the strided selection (else 0)
     int stride_m;           // PCH_CONTROL_STRIDED: windows each of them selects (1, 2, 4, 8 or 16)
+    int prov;               // record distance events for geodesic paths
     const float* mlp;
 };
 
@@ -37,7 +38,10 @@ int default_prop_blocks_per_sm(int block);
 int default_tail_cut();
 const float* mlp_device_params();
 
+// prov: also record every distance event that lowered a vertex's distance (geodesic
+// paths); the records stay in the workspace after the call.
 pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* srcs, int n_src,
-                           const pch_options* opt, double* const* outs, int out_mode, pch_stats* stats);
+                           const pch_options* opt, double* const* outs, int out_mode, pch_stats* stats,
+                           int prov = 0);
 
 }  // namespace pch

@@ -35,6 +35,14 @@ class Source(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("bary", ctypes.c_double * 3)]
 
 
+class PathPoint(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("id", ctypes.c_int32), ("t0", ctypes.c_double), ("t1", ctypes.c_double)]
+
+
+PATH_POINT_DTYPE = np.dtype([("kind", np.int32), ("id", np.int32), ("t0", np.float64), ("t1", np.float64)])
+POINT_VERTEX, POINT_EDGE, POINT_FACE = 0, 1, 2
+
+
 class Options(ctypes.Structure):
     _fields_ = [("control", ctypes.c_int32), ("loop", ctypes.c_int32), ("k", ctypes.c_int64),
                 ("max_iters", ctypes.c_int64), ("stream", ctypes.c_void_p), ("out_on_device", ctypes.c_int32),
@@ -82,6 +90,7 @@ def _load():
         "pch_measure_fp64_peak": (I32, [P]),
         "pch_autotune": (I32, [P, P, P, ctypes.c_char_p, P]),
         "pch_selftest_math": (I32, [P, I32, P]),
+        "pch_trace_paths": (I32, [P, P, I32, P, P, I32, I32, P, P, P, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -196,6 +205,39 @@ def solve_batch(meshes, sources, *, outs=None, stats=False, **opts):
     st = Stats()
     _check(lib.pch_solve_batch(handles, srcs, n, ctypes.byref(o), ptrs, ctypes.byref(st)))
     return (res, st.as_dict()) if stats else res
+
+
+def trace_paths(mesh: Mesh, sources, targets, *, face=None, bary=None, max_points: int = 4096, stats=False, **opts):
+    """Exact geodesic paths (pch_trace_paths) from vertex ``sources`` (a list), or from
+    the point of ``face`` with barycentric ``bary`` when sources is None, to each vertex of
+    ``targets``.  Returns (dist, paths): paths[i] is None when the trace failed, else a
+    tuple (kind, id, t0, t1) of arrays, target first (an empty path for an unreachable
+    target).  Raises if a path has more than max_points points."""
+    if sources is None:
+        src_list = [make_source(face=face, bary=bary)]
+    else:
+        src_list = [make_source(s) for s in sources]
+    srcs = (Source * len(src_list))(*src_list)
+    tg = np.ascontiguousarray(targets, dtype=np.int32)
+    nt = int(tg.shape[0])
+    pts = np.zeros((max(nt, 1), max_points), dtype=PATH_POINT_DTYPE)
+    n = np.zeros(max(nt, 1), dtype=np.int32)
+    dist = np.empty(mesh.nv, dtype=np.float64)
+    o = make_options(**opts)
+    st = Stats()
+    _check(lib.pch_trace_paths(mesh.handle, srcs, len(src_list), ctypes.byref(o), tg.ctypes.data, nt, max_points,
+                               pts.ctypes.data, n.ctypes.data, dist.ctypes.data, ctypes.byref(st)))
+    paths = []
+    for i in range(nt):
+        k = int(n[i])
+        if k < 0:
+            paths.append(None)
+            continue
+        if k > max_points:
+            raise PchError(PCH_ERR_CAPACITY, f"path {i} has {k} points, more than max_points={max_points}")
+        p = pts[i, :k]
+        paths.append((p["kind"].copy(), p["id"].copy(), p["t0"].copy(), p["t1"].copy()))
+    return (dist, paths, st.as_dict()) if stats else (dist, paths)
 
 
 def mlp_num_features() -> int:
