@@ -32,6 +32,19 @@ def path_xyz(vertices, faces, path):
     return np.array([point_xyz(vertices, faces, k, i, a, b) for k, i, a, b in zip(kinds, ids, t0, t1)])
 
 
+_MAPS = {}
+
+
+def _maps(faces):
+    """Vertex -> faces and edge -> faces of a face array (cached per array content)."""
+    key = (faces.shape, hash(np.ascontiguousarray(faces).tobytes()))
+    if key not in _MAPS:
+        if len(_MAPS) > 16:
+            _MAPS.clear()
+        _MAPS[key] = (vertex_faces(faces), edge_faces(faces))
+    return _MAPS[key]
+
+
 def vertex_faces(faces):
     vf = {}
     for f, tri in enumerate(faces):
@@ -97,7 +110,7 @@ def check_path(vertices, faces, dist, target, path, sources=None, face_source=No
     for j in range(n):
         if kinds[j] == 0:
             assert abs(rem[j] - dist[ids[j]]) <= rel * scale, (j, rem[j], dist[ids[j]])
-    vf, ef = vertex_faces(faces), edge_faces(faces)
+    vf, ef = _maps(faces)
     for j in range(n - 1):
         a = faces_of(faces, vf, ef, kinds[j], ids[j], t0[j])
         b = faces_of(faces, vf, ef, kinds[j + 1], ids[j + 1], t0[j + 1])
