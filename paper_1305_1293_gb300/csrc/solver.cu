@@ -52,7 +52,6 @@ __device__ __forceinline__ unsigned long long pack_angle(double D, double xq) {
 }
 // kEpsSnap in angle_split units (the snap tolerance kEpsSnap * L times 2^24 / L).
 constexpr double kSplitTol = kEpsSnap * (double)(1 << kAngleXBits);
-constexpr double kAngleScale = (double)(1 << kAngleXBits);
 
 struct WarpScan {
     int excl, total;
@@ -657,8 +656,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
 
 // Windows in flight per block: the shared-memory queue of chained children holds at most
 // one window per thread, in two buffers (read / written by alternate rounds) of 7 doubles
-// and 4 ints per entry.
-constexpr int kPropMaxBlock = 256;
+// and 4 ints per entry (blocks of at most 256 threads: 36 KB).
 constexpr int kPropQueueBytesPerThread = 2 * (7 * 8 + 4 * 4);
 
 // Step 3 of the iteration (Algorithm 2 over the selected windows), persistent.  The block
