@@ -4,7 +4,9 @@ The oracle traces a path back along the window sequence that gave the target its
 distance (Section 4.4) as straight unfolded segments between pseudo-sources (Section 3).
 Pinned here by what fixes a geodesic independently of that code:
 
-* on a convex plane patch the path is the straight chord from the source;
+* on a convex plane patch the path is the straight chord from the source, and on a
+  prism tube unrolled onto its periodic strip a straight segment of the closed-form
+  length;
 * on brute-force meshes (exhaustive unfolding, tests/bruteforce.py) its length is the
   brute-force distance;
 * on every mesh it passes the geometric checks of tests/pathcheck.py (starts at the
@@ -62,6 +64,56 @@ def test_plane_face_point_paths(oracle_lib):
         xyz = pc.path_xyz(m.vertices, m.faces, p)
         assert np.linalg.norm(xyz[-1] - p0) < 1e-12
         assert np.max(_line_dev(xyz, p0, m.vertices[t])) < 1e-12
+
+
+def _prism_unroll(m, sides, perim, xyz):
+    """Unrolled (s, z) of points on a prism tube's lateral surface, continuous along the
+    sequence (a jump across the seam adds or removes the perimeter)."""
+    c = m.vertices[:sides, :2]
+    nxt = np.roll(c, -1, axis=0)
+    seg = np.linalg.norm(nxt - c, axis=1)
+    s0 = np.concatenate([[0.0], np.cumsum(seg)[:-1]])
+    out, prev = [], None
+    for p in xyz:
+        best = None
+        for k in range(sides):
+            u = (nxt[k] - c[k]) / seg[k]
+            r = p[:2] - c[k]
+            along = float(r @ u)
+            off = abs(float(r[0] * u[1] - r[1] * u[0]))
+            if -1e-12 <= along <= seg[k] + 1e-12 and (best is None or off < best[0]):
+                best = (off, s0[k] + along)
+        assert best is not None and best[0] < 1e-9
+        sv = best[1]
+        if prev is not None:
+            sv += perim * round((prev - sv) / perim)
+        out.append((sv, p[2]))
+        prev = sv
+    return np.array(out)
+
+
+@pytest.mark.parametrize("sides,rings,seed,src", [(7, 4, 0, 0), (11, 6, 1, 30), (5, 9, 2, 24)])
+def test_prism_paths_are_straight_unrolled(oracle_lib, sides, rings, seed, src):
+    """Unrolled onto the periodic strip, every path is one straight segment whose length
+    is the closed-form distance (the wrap-around copy of the source it ends at)."""
+    m, s, z, perim = mg.prism_tube(sides, rings, height=1.5, seed=seed)
+    tg = np.arange(m.nv)
+    d, paths = oracle_lib.trace_paths(m.vertices, m.faces, src, targets=tg)
+    ds, dz = s - s[src], z - z[src]
+    ex = np.min([np.hypot(ds + k * perim, dz) for k in (-1, 0, 1)], axis=0)
+    for t, p in zip(tg, paths):
+        pc.check_path(m.vertices, m.faces, d, t, p, sources=[src])
+        if t == src:
+            continue
+        uv = _prism_unroll(m, sides, perim, pc.path_xyz(m.vertices, m.faces, p))
+        a, b = uv[0], uv[-1]
+        assert abs(np.linalg.norm(b - a) - ex[t]) <= 1e-12 * max(ex[t], 1.0)
+        # crossing points within 1e-10 of the segment: the oracle's (d0, d1) windows give the
+        # pseudo-source's height through d0^2 - px^2, which loses digits when the source is
+        # far from a short edge (a wrong crossing would be off by a face's size)
+        u = (b - a) / np.linalg.norm(b - a)
+        dev = np.abs((uv - a) @ np.array([-u[1], u[0]]))
+        assert np.max(dev) <= 1e-10 * max(ex[t], 1.0), (t, np.max(dev))
 
 
 TINY = [
