@@ -537,11 +537,13 @@ struct Solver {
 
     int run(const int* targets, int n_targets) {
         Entry en;
-        while (true) {
-            if (n_targets > 0) {
+        for (long long pops = 0;; ++pops) {
+            // every 1024 windows (the scan costs n_targets): stop once the targets are
+            // final (keys never decrease); stopping later only propagates more windows
+            if (n_targets > 0 && (pops & 1023) == 0) {
                 double gmax = 0;
                 for (int i = 0; i < n_targets; ++i) gmax = std::max(gmax, g[targets[i]]);
-                if (min_key() >= gmax) break;   // keys never decrease: targets are final
+                if (min_key() >= gmax) break;
             }
             if (!pop(en)) break;
             if (stale(en.w)) continue;
