@@ -15,6 +15,9 @@
 //    new windows.  Being sequential, events are applied at once (no event sort needed).
 //  * initialisation per Algorithm 1: geod_dist = 0 at the source, +inf elsewhere; one
 //    window on every edge opposite the source (Section 4.2, "Initialization").
+//  * geodesic paths (TRACE): every window keeps its parent and its pseudo-source vertex,
+//    every vertex the event that set its distance; a path is walked back along that
+//    window sequence (Section 4.4) as straight unfolded segments (Section 3).
 // Readings where the paper is silent (tolerances, which child a losing window keeps,
 // boundary vertices, face-point sources) are stated next to the code that takes them.
 #include <algorithm>
