@@ -474,6 +474,42 @@ def run_paths(args):
     h.close()
 
 
+NCU_CASES = {
+    # name: (mesh builder, sources, solve options) - one solve each, host-driven loop, so
+    # that every phase kernel is its own launch and the k-th k_propagate launch is the
+    # k-th iteration's
+    "terrain256": (lambda mg: mg.terrain(256, 256, seed=mg.SEED_BASE + 1), lambda mg, m: [mg.terrain_center(256, 256)],
+                   {"k": 393216, "hops": 32, "block": 64}),
+    "terrain512": (lambda mg: mg.workload("terrain", "full")[0][0], lambda mg, m: [mg.terrain_center(512, 512)],
+                   {"k": 393216, "hops": 32, "block": 64}),
+    "sphere7x8": (lambda mg: mg.multi_octave_sphere(7, 0.05, seed=mg.SEED_BASE + 5),
+                  lambda mg, m: [int(x) for x in mg.pick_sources(m, 8, mg.SEED_BASE + 105)],
+                  {"k": 1 << 20, "hops": 64, "block": 64}),
+}
+
+
+def run_ncu_case(args):
+    """One solve of a small named case with the host-driven loop, for ncu captures (never
+    a bench value: nothing is timed here)."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1305_1293_gb300 import meshgen as mg, pch
+    make, srcs, opts = NCU_CASES[args.ncu_case]
+    m = make(mg)
+    sv = srcs(mg, m)
+    h = pch.Mesh(m.vertices, m.faces)
+    if len(sv) == 1:
+        _, st = pch.solve(h, sv[0], stats=True, loop=pch.LOOP_HOST, **opts)
+    else:
+        _, st = pch.solve_batch([h] * len(sv), sv, stats=True, loop=pch.LOOP_HOST, **opts)
+    print(json.dumps({"ncu_case": args.ncu_case, "faces": m.nf, "sources": len(sv), "opts": opts,
+                      "iterations": st["iterations"], "windows_propagated": st["windows_propagated"],
+                      "kernel_launches": st["kernel_launches"], "prop_fp64_ops": st["prop_fp64_ops"]}), flush=True)
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -487,8 +523,12 @@ def main():
                     help="terrain = the benchmark line; others print a per-workload report line")
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="iteration driver: CUDA graph with device-side termination, or host-driven (for ncu)")
+    ap.add_argument("--ncu-case", default=None, choices=sorted(NCU_CASES),
+                    help="run one untimed solve of a small case for an ncu capture")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.ncu_case:
+        run_ncu_case(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "paths":
         run_paths(args)

@@ -59,7 +59,10 @@ typedef struct {
 enum {
     PCH_CONTROL_PLAIN = 0,    /* fixed window count k per iteration (the paper's k) */
     PCH_CONTROL_LEARNED = 1,  /* MLP controller maps frontier statistics to the threshold;
-                                 falls back to PLAIN on a non-finite or out-of-range output */
+                                 falls back to PLAIN on a non-finite or out-of-range output,
+                                 and runs PLAIN when no weights were installed
+                                 (pch_mlp_set_weights) on the current device since its
+                                 CUDA context was created */
     PCH_CONTROL_STRIDED = 2   /* the paper's approximate k-selection of Section 5.1: T threads
                                  each take every T-th pending window and select their
                                  ceil(k / T) nearest, about k windows per instance in total.
@@ -203,6 +206,49 @@ pch_status pch_trace_paths(pch_mesh* m, const pch_source* srcs, int32_t n_source
                            const int32_t* targets, int32_t n_targets, int32_t max_points,
                            pch_path_point* points, int32_t* n_points, double* out_dist, pch_stats* stats);
 
+/* ---- geodesic Voronoi diagram (Section 7: the multiple-source field applied to the
+ * geodesic Voronoi diagram) ------------------------------------------------------------
+ * Labels every vertex with the index (into srcs) of its nearest source.  Solves the field
+ * as pch_solve_multi does while recording the distance events (as pch_trace_paths does);
+ * a vertex's final event names the last pseudo-source vertex of its shortest path
+ * (Section 3: geodesics bend only at saddle or boundary vertices), or the face-point
+ * source itself, and the chain of those vertices, whose distances strictly decrease,
+ * ends at the source that labels the vertex.  Where two sources are equally near (within
+ * rounding) either label may be returned.  labels (host, n_vertices): the source index,
+ * -1 for a vertex no source reaches, -2 if a vertex's chain could not be followed (no
+ * recorded event carries its final distance; not expected).  out_dist (host, n_vertices)
+ * may be NULL.  opt as for pch_solve_multi, except that out_on_device is ignored.
+ * Errors: as pch_solve_multi. */
+pch_status pch_voronoi(pch_mesh* m, const pch_source* srcs, int32_t n_sources, const pch_options* opt,
+                       int32_t* labels, double* out_dist, pch_stats* stats);
+
+/* ---- iso-contours ----------------------------------------------------------------------
+ * A segment of the iso-contour of level levels[level] inside face `face`: from the point
+ * at fraction t[0] along half-edge half_edge[0] to the point at fraction t[1] along
+ * half_edge[1] (half-edge 3 f + i runs from corner i to corner (i + 1) % 3 of face f; the
+ * fraction is measured from its start).  Seen from the face's front side (corners
+ * counter-clockwise) the region below the level lies to the left of the segment. */
+typedef struct {
+    int32_t level;
+    int32_t face;
+    int32_t half_edge[2];
+    double t[2];
+} pch_contour_segment;
+
+/* Iso-contours of a distance field (the iso-contours of geodesic distance that Section 2
+ * cites as a use of exact distances), one straight segment per face and level.  On each
+ * face the field is the linear interpolation of its three vertex distances: a vertex is
+ * below a level L when its distance is < L, and the contour crosses every edge whose two
+ * ends are on different sides at the interpolated point t = (L - d_start) / (d_end -
+ * d_start).  Faces with a non-finite vertex distance have no segment.  dist: n_vertices
+ * doubles (a field from pch_solve), a device pointer if dist_on_device else host; levels:
+ * n_levels finite doubles (host).  Segments are ordered by face, then by level index.
+ * *n_segments gets the total count; the first min(total, capacity) segments are written
+ * to segments (host), so a call with capacity 0 only counts.  Errors: INVALID_ARG,
+ * CAPACITY (more than 2^31 - 1 segments), OOM, CUDA. */
+pch_status pch_iso_contours(const pch_mesh* m, const double* dist, int32_t dist_on_device, const double* levels,
+                            int32_t n_levels, pch_contour_segment* segments, int64_t capacity, int64_t* n_segments);
+
 /* Release a mesh and its workspace (NULL is a no-op). */
 void pch_destroy(pch_mesh* m);
 
@@ -215,7 +261,9 @@ const char* pch_last_error(void);
  * (layer by layer: W then b, W row-major [out][in]). */
 int32_t pch_mlp_num_features(void);
 int32_t pch_mlp_num_params(void);
-/* Install weights used by PCH_CONTROL_LEARNED (host array, copied). */
+/* Install weights used by PCH_CONTROL_LEARNED on the current device (host array, copied
+ * to a device buffer the library keeps for that device's current CUDA context; call it on
+ * every device that runs learned solves, and again after a device reset). */
 pch_status pch_mlp_set_weights(const float* params, int32_t n_params);
 /* Forward pass on the device: x (n x num_features), y (n) device pointers. */
 pch_status pch_mlp_forward(const float* params_dev, const float* x_dev, int32_t n, float* y_dev,
@@ -230,8 +278,9 @@ pch_status pch_mlp_backward(const float* params_dev, const float* x_dev, const f
  * There is no counterpart in the paper.  Its scratch is one fixed device array of the
  * library (6.3 MB, held on every GPU that loads the library until exit), so n is
  * limited to 4096 samples; a larger n returns PCH_ERR_CAPACITY and computes nothing.
- * The first call on a device looks the array up for that device; make that first call
- * before any stream capture.  All calls share the array: calls whose work overlaps on
+ * The first call on a device (and the first after its CUDA context was replaced, e.g. by
+ * cudaDeviceReset) looks the array up for that device; make that first call before any
+ * stream capture.  All calls share the array: calls whose work overlaps on
  * the GPU (other threads, other streams) race and must be serialised by the caller.
  * Nothing in the array needs clearing between calls. */
 pch_status pch_mlp_backward_noalloc(const float* params_dev, const float* x_dev, const float* target_dev,
@@ -246,18 +295,26 @@ pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float
                            int32_t* n_rows);
 
 /* ---- autotuner (build-only) ------------------------------------------------------------
- * Times full solves of `src` on `m` by a coordinate search: windows-per-iteration k
- * (24576 times powers of 4, up to 8x the face count, from the largest down until one is twice
- * as slow as the best) at block 128 and 16 hops, then hops
- * (4, 8, 16, 32, 64), then propagation block sizes (64, 128, 256), and writes the fastest
- * into opt->k, opt->block and opt->hops (the other fields of *opt are kept and used for
- * every trial).  If cache_path is not NULL the result is looked up first in, and then
- * appended to, that text file, keyed by GPU name and mesh size, so a
- * second call does no timing.  Errors: as pch_solve. */
+ * Times full solves of `src` on `m`: first the library defaults (k 24576, block 64, 32
+ * hops), then a coordinate search over windows-per-iteration k (24576 times powers of 4,
+ * up to 8x the face count, from the largest down until one is twice as slow as the best)
+ * at block 128 and 16 hops, then hops (4, 8, 16, 32, 64), then propagation block sizes
+ * (64, 128, 256); under PCH_CONTROL_LEARNED (the network picks k every iteration) only
+ * hops and the block size are searched.  Each trial is timed on its second solve (the
+ * first builds its graph).
+ * Writes the fastest into opt->k, opt->block and opt->hops (the other fields of *opt are
+ * kept and used for every trial) and its time into *best_ms (may be NULL).  If
+ * cache_path is not NULL the result is looked up first in, and then appended to, that
+ * text file, keyed by GPU name, library build id (pch_build_id), mesh size, control and
+ * flags, so a second call with the same library does no timing.  Errors: as pch_solve. */
 pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_options* opt, const char* cache_path,
                         double* best_ms);
 
 /* ---- measurement helpers ---------------------------------------------------------- */
+/* Build id of the library: the first 16 hex digits of the SHA-256 of its sources (a
+ * static string owned by the library). */
+const char* pch_build_id(void);
+
 /* Accuracy check of the library's FP64 reciprocal and square root (Newton-Raphson from a
  * single-precision estimate) against IEEE 1/x and sqrt(|x|) on n device doubles x_dev:
  * max_ulp_host[0], [1] get the largest distance in units in the last place. */

@@ -2,6 +2,7 @@
 from __future__ import annotations
 
 import concurrent.futures
+import hashlib
 import os
 import subprocess
 
@@ -9,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpch.so")
-SOURCES = ["mesh.cu", "radix.cu", "solver.cu", "controller.cu"]
+SOURCES = ["mesh.cu", "radix.cu", "solver.cu", "controller.cu", "contour.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
 
@@ -27,18 +28,33 @@ def _stale(out, deps):
     return any(os.path.getmtime(d) > t for d in deps)
 
 
+def build_id(files) -> str:
+    """First 16 hex digits of the SHA-256 of the library's sources: compiled in as
+    PCH_BUILD_ID, it keys the autotuner's cache so that timings taken with other kernels
+    are never reused."""
+    h = hashlib.sha256()
+    for f in sorted(files):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(os.path.dirname(HERE), "include", "pch.h"))
+    bid = build_id(headers + [os.path.join(CSRC, s) for s in SOURCES])
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
-        if force or _stale(o, [s] + headers):
-            jobs.append([_nvcc(), *NVCC_FLAGS, "-c", s, "-o", o])
+        # the autotuner (solver.cu) carries the build id of every source
+        deps = [s] + headers + ([os.path.join(CSRC, x) for x in SOURCES] if src == "solver.cu" else [])
+        if force or _stale(o, deps):
+            jobs.append([_nvcc(), *NVCC_FLAGS, f"-DPCH_BUILD_ID=\"{bid}\"", "-c", s, "-o", o])
 
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)

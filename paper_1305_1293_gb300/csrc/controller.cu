@@ -2,9 +2,9 @@
 // and the FP64 peak microbenchmark.  The network and its role are described in
 // controller.cuh; none of this has a counterpart in the paper, which fixes k by hand
 // (Section 5.2).
-#include <atomic>
 #include <cmath>
 #include <cstdlib>
+#include <mutex>
 #include <vector>
 
 #include "pch_host.h"
@@ -12,10 +12,26 @@
 
 namespace pch {
 
-static float* g_mlp_dev = nullptr;   // installed weights (device), used by PCH_CONTROL_LEARNED
-static int g_mlp_dev_id = -1;
+// Installed controller weights, one device buffer per device, each valid only in the
+// context it was allocated in (a reset device loses its weights).
+constexpr int kMaxDevices = 64;
+struct DevPtrSlot {
+    unsigned long long ctx = 0;   // current_context_id() when ptr was obtained; 0 = empty
+    float* ptr = nullptr;
+};
+static DevPtrSlot g_mlp_slot[kMaxDevices];
+static std::mutex g_mlp_mu;
 
-const float* mlp_device_params() { return g_mlp_dev; }
+// The current device's weights, or nullptr when none were installed in its current
+// context: PCH_CONTROL_LEARNED then runs the plain control.
+const float* mlp_device_params() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+    const unsigned long long ctx = current_context_id();
+    std::lock_guard<std::mutex> lk(g_mlp_mu);
+    const DevPtrSlot& sl = g_mlp_slot[dev];
+    return (ctx != 0 && sl.ctx == ctx) ? sl.ptr : nullptr;
+}
 
 long long default_k() {
     const char* e = std::getenv("PCH_DEFAULT_K");
@@ -208,13 +224,20 @@ extern "C" pch_status pch_mlp_set_weights(const float* params, int32_t n_params)
     for (int i = 0; i < n_params; ++i)
         if (!std::isfinite(params[i])) return set_error(PCH_ERR_INVALID_ARG, "non-finite weight %d", i);
     int dev = 0;
-    cudaGetDevice(&dev);
-    if (g_mlp_dev && g_mlp_dev_id != dev) g_mlp_dev = nullptr;   // other device: reallocate
-    if (!g_mlp_dev) {
-        PCH_CUDA(cudaMalloc(&g_mlp_dev, sizeof(float) * kMlpParams));
-        g_mlp_dev_id = dev;
+    PCH_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return set_error(PCH_ERR_INVALID_ARG, "device id %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_mlp_mu);
+    DevPtrSlot& sl = g_mlp_slot[dev];
+    unsigned long long ctx = current_context_id();
+    if (ctx == 0 || sl.ctx != ctx) {
+        // first weights in this device's current context (a buffer of an earlier, destroyed
+        // context is gone with it and is not freed)
+        float* p = nullptr;
+        PCH_CUDA(cudaMalloc(&p, sizeof(float) * kMlpParams));
+        sl.ptr = p;
+        sl.ctx = current_context_id();   // the allocation made the context current
     }
-    PCH_CUDA(cudaMemcpy(g_mlp_dev, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice));
+    PCH_CUDA(cudaMemcpy(sl.ptr, params, sizeof(float) * kMlpParams, cudaMemcpyHostToDevice));
     return PCH_OK;
 }
 
@@ -297,10 +320,11 @@ constexpr int kNoAllocMaxSamples = 4096;
 constexpr size_t kNoAllocActFloats = (size_t)kNoAllocMaxSamples * 3 * kHidden;
 constexpr size_t kNoAllocFloats = 2 * kNoAllocActFloats + 2 * (size_t)kNoAllocMaxSamples;
 static __device__ __align__(256) float g_noalloc_scratch[kNoAllocFloats];
-constexpr int kNoAllocMaxDevices = 64;
-// Host side: the array's device address, resolved once per device.  The symbol itself
-// is only a host-side stand-in and must never be handed to a kernel.
-static std::atomic<float*> g_noalloc_addr[kNoAllocMaxDevices];
+// Host side: the array's device address, resolved once per device and context (a reset
+// device gets a new context, and the array a new address).  The symbol itself is only a
+// host-side stand-in and must never be handed to a kernel.
+static DevPtrSlot g_noalloc_slot[kMaxDevices];
+static std::mutex g_noalloc_mu;
 }  // namespace pch
 
 extern "C" pch_status pch_mlp_backward_noalloc(const float* params_dev, const float* x_dev, const float* target_dev,
@@ -313,17 +337,26 @@ extern "C" pch_status pch_mlp_backward_noalloc(const float* params_dev, const fl
                          kNoAllocMaxSamples, n);
     int dev = 0;
     PCH_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return set_error(PCH_ERR_INVALID_ARG, "device id %d out of range", dev);
-    float* scratch = g_noalloc_addr[dev].load();
-    if (!scratch) {
-        // first call on this device (the device is current): look the array up
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || p == nullptr)
-            return set_error(PCH_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
-                             cudaGetErrorString(e));
-        scratch = static_cast<float*>(p);
-        g_noalloc_addr[dev].store(scratch);
+    if (dev < 0 || dev >= kMaxDevices) return set_error(PCH_ERR_INVALID_ARG, "device id %d out of range", dev);
+    float* scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        DevPtrSlot& sl = g_noalloc_slot[dev];
+        const unsigned long long ctx = current_context_id();
+        if (ctx != 0 && sl.ctx == ctx) {
+            scratch = sl.ptr;
+        } else {
+            // first call on this device in its current context (the device is current):
+            // look the array up
+            void* p = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+            if (e != cudaSuccess || p == nullptr)
+                return set_error(PCH_ERR_CUDA, "cudaGetSymbolAddress of the scratch array failed: %s",
+                                 cudaGetErrorString(e));
+            scratch = static_cast<float*>(p);
+            sl.ptr = scratch;
+            sl.ctx = current_context_id();
+        }
     }
     cudaStream_t s = (cudaStream_t)stream;
     float* act = scratch;

@@ -59,9 +59,13 @@ __device__ __forceinline__ double rcp_nr(double x) {
     return fma(r, e, r);
 }
 
-// sqrt(x), coupled iteration on g ~ sqrt(x) and h ~ 1 / (2 sqrt(x)) from the
-// seed y ~ 1/sqrt(x): g = x y, h = y / 2, r = 1/2 - g h, g += g r, h += h r (both now
-// good to about 2^-40), then one Newton correction g + (x - g^2) h.
+// sqrt(x) by Goldschmidt's coupled iteration for the square root as given by P.
+// Markstein, "Software Division and Square Root Using Goldschmidt's Algorithms" (Proc.
+// 6th Conference on Real Numbers and Computers, 2004), and in his "IA-64 and Elementary
+// Functions" (Prentice Hall, 2000): g ~ sqrt(x) and h ~ 1 / (2 sqrt(x)) from the seed
+// y ~ 1/sqrt(x): g = x y, h = y / 2, r = 1/2 - g h, g += g r, h += h r (both now good to
+// about 2^-40), then one Newton correction of the residual, g + (x - g^2) h.  The
+// reciprocal above is the classical Newton-Raphson iteration r' = r + r (1 - x r).
 __device__ __forceinline__ double sqrt_nr(double x) {
     if (!nr_range_pos(x)) return sqrt(x);
     const float y = rsqrt_approx_f32(narrow_seed(x));

@@ -137,8 +137,12 @@ struct Counters {
     unsigned long long examined, occupied, children, rays;   // propagation path counts (FP64 op tally)
     unsigned long long scanned, sorted;               // windows read by compaction / sorted
     int work_next;          // next work-list index handed to a propagation lane
-    int n_plog;             // provenance records written (geodesic paths)
+    int n_plog;             // unused (kept for the layout); see n_plog_shard
+    int n_plog_shard[32];   // provenance records reserved per shard (geodesic paths)
 };
+// Distance-event records are split into kPlogShards equal shards, one counter each, chosen
+// by the SM a warp runs on: slot reservations then contend on 32 counters, not one.
+constexpr int kPlogShards = 32;
 
 enum : int {
     kErrPoolFull = 1,

@@ -45,4 +45,10 @@ cudaError_t exclusive_scan(const int* in, int* out, int n, int* tmp, cudaStream_
 // Number of SMs of the current device (cached).
 int sm_count();
 
+// Unique id of the calling thread's current CUDA context, 0 if there is none (or the
+// driver cannot tell).  Device pointers the library caches across calls are keyed on it,
+// so that a pointer from a context that has since been destroyed (cudaDeviceReset, a new
+// primary context) is never used again.
+unsigned long long current_context_id();
+
 }  // namespace pch

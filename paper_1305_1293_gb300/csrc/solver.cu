@@ -93,13 +93,32 @@ struct EvSrc {
     double px, py;
 };
 
+__device__ __forceinline__ unsigned sm_id() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(r));
+    return r;
+}
+
+// Record one distance event.  The lanes of the warp that record at the same time reserve
+// their slots with one atomic (opportunistic warp aggregation over the active lanes), on
+// the counter of the shard of the SM the warp runs on; shard r owns records
+// [r * per, (r + 1) * per), per = plog_cap / kPlogShards.
 __device__ __forceinline__ void log_event(const Work& w, const EvSrc& es, unsigned v, unsigned long long db) {
-    const int slot = atomicAdd(&w.cnt->n_plog, 1);
-    if (slot < w.plog_cap) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(mask) - 1;
+    const int rank = __popc(mask & ((1u << lane) - 1u));
+    const int shard = (int)(sm_id() & (kPlogShards - 1));
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&w.cnt->n_plog_shard[shard], __popc(mask));
+    base = __shfl_sync(mask, base, leader);
+    const int slot = base + rank;
+    const int per = w.plog_cap / kPlogShards;
+    if (slot < per) {
         ProvRec r;
         r.db = db; r.inst = es.inst; r.v = (int)v; r.h = es.h; r.src = es.src; r.kind = es.kind; r.pad = 0;
         r.px = es.px; r.py = es.py;
-        w.plog[slot] = r;
+        w.plog[(size_t)shard * per + slot] = r;
     } else {
         atomicOr(&w.cnt->error, kErrProvFull);
     }
@@ -158,7 +177,7 @@ struct PoolStats {
     unsigned* g_hist;
     int n_inst;
 };
-constexpr int kShHistInst = 8;
+constexpr int kShHistInst = 32;      // 32 KB of shared memory per block
 
 __device__ __forceinline__ void pool_stat(const Work& w, const PoolStats& ps, int inst, double key, bool on) {
     // minimum key per instance: warp-reduce when the warp holds a single instance
@@ -185,8 +204,14 @@ __device__ __forceinline__ void pool_stat(const Work& w, const PoolStats& ps, in
     if (on) {
         const InstCtl& c = w.ctl[inst];
         int b = hist_bin(key, c.ref, w.inst[inst].ilbar);
-        if (ps.sh_hist) atomicAdd(&ps.sh_hist[inst * kBins + b], 1u);
-        else atomicAdd(&ps.g_hist[inst * kBins + b], 1u);
+        if (ps.sh_hist) {
+            atomicAdd(&ps.sh_hist[inst * kBins + b], 1u);
+        } else {
+            // many instances: lanes that hit the same global bin add together
+            const int slot = inst * kBins + b;
+            const unsigned peers = __match_any_sync(__activemask(), slot);
+            if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(&ps.g_hist[slot], (unsigned)__popc(peers));
+        }
     }
 }
 
@@ -248,7 +273,7 @@ __global__ void k_init_face_sources(Work w, const SrcDev* __restrict__ srcs, int
             double x = b1 * R.L + b2 * R.xc, y = b2 * R.yc;        // point in h's frame
             double dstart = sqrt(x * x + y * y);
             double gc = ldg_dist(I.g, R.v0 & ~kPseudoBit);
-            const EvSrc es{s.inst, h, -1, 2, x, y};
+            const EvSrc es{s.inst, h, -1 - s.label, 2, x, y};
             if (w.plog ? vertex_event<true>(I, R.v0, dstart, gc, &w, &es) : vertex_event(I, R.v0, dstart, gc)) {
                 // incoming direction: from the corner towards the point, inside face(h)
                 push_fan(w.req[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, R.v0 & ~kPseudoBit, dstart, h, x, y);
@@ -259,7 +284,7 @@ __global__ void k_init_face_sources(Work w, const SrcDev* __restrict__ srcs, int
             const double IA = sqrt(px * px + py * py), IB = sqrt((px - R.L) * (px - R.L) + py * py);
             double key = px < 0 ? IA : (px > R.L ? IB : -py);
             int slot = atomicAdd(&cnt->n_child, 1);
-            if (slot < w.arena_cap) store_win(w.arena, slot, R.twin, s.inst, 0.0, 0.0, R.L, px, py, key, -1, IA, IB);
+            if (slot < w.arena_cap) store_win(w.arena, slot, R.twin, s.inst, 0.0, 0.0, R.L, px, py, key, -1 - s.label, IA, IB);
         }
     }
 }
@@ -654,19 +679,21 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
     return prop;
 }
 
-// Windows in flight per block: the shared-memory queue of chained children holds at most
-// one window per thread, in two buffers (read / written by alternate rounds) of 7 doubles
+// Windows in flight per warp: the shared-memory queue of chained children holds at most
+// one window per lane, in two buffers (read / written by alternate rounds) of 7 doubles
 // and 4 ints per entry (blocks of at most 256 threads: 36 KB).
 constexpr int kPropQueueBytesPerThread = 2 * (7 * 8 + 4 * 4);
+constexpr int kPropMaxWarps = 8;      // warps per block at most (256 threads)
 
-// Step 3 of the iteration (Algorithm 2 over the selected windows), persistent.  The block
-// advances in lock-step rounds: in each round lane t takes queue entry t (a child chained
-// from the previous round, key <= tau, at most `hops` hops from its selected ancestor) or
-// else a fresh selected window; children that continue are pushed back into the queue
-// (chaining stops while the child arena is half full).
-// Repacking the chains onto the lowest lanes every round keeps the warps that do issue
-// FP64 work full once the selected list runs dry, and leaves the other warps idle.
-// 168 registers a thread at most (148 used, no spills): 6 blocks of 64 threads per SM.
+// Step 3 of the iteration (Algorithm 2 over the selected windows), persistent.  Every
+// warp advances on its own in rounds: in each round lane t takes entry t of the warp's
+// queue (a child chained from the warp's previous round, key <= tau, at most `hops` hops
+// from its selected ancestor) or else a fresh selected window; children that continue
+// are pushed back into the warp's queue (chaining stops while the child arena is half
+// full).  Repacking the chains onto the warp's lowest lanes every round keeps the lanes
+// that issue FP64 work together; no warp waits for another (only __syncwarp between
+// rounds), and a warp leaves once the selected list is exhausted and its queue is empty.
+// 168 registers a thread at most (152 used, no spills): 6 blocks of 64 threads per SM.
 // PROV: also record the distance events (geodesic paths).
 template <bool PROV>
 __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
@@ -683,16 +710,13 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
     int* q_inst = q_he + QB;
     int* q_src = q_inst + QB;
     int* q_hop = q_src + QB;
-    // Round r reads s_nq[r % 3] / s_dry[r % 3], writes slot (r + 1) % 3 and clears slot
-    // (r + 2) % 3 (read in round r - 1, written in round r + 1), so no slot is written in
-    // the round that reads it and every decision taken from them is uniform over the block.
-    __shared__ int s_nq[3];      // queue sizes
-    __shared__ int s_dry[3];     // the selected list is exhausted
+    // per warp and buffer: entries written (by the round that writes that buffer)
+    __shared__ int s_cnt[kPropMaxWarps][2];
     Counters* cnt = w.cnt;
     if (cnt->halt) return;
     const unsigned full = 0xffffffffu;
-    const int t = threadIdx.x;
-    const int lane = t & 31;
+    const int lane = threadIdx.x & 31;
+    const int wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int it = cnt->iter;
     const int n = min(cnt->n_sel, w.sel_cap);
@@ -701,46 +725,34 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
     // the arena fill this warp last saw (updated whenever it reserves arena slots): a
     // warp overshoots the room by at most one round of its own writes
     int seen_child = *(volatile int*)&cnt->n_child;
-    // statistics, kept per thread and added to the counters once when the block ends
+    // statistics, kept per thread and added to the counters once when the warp ends
     unsigned n_prop = 0, n_chain = 0, n_exam = 0, n_occ = 0, n_comp = 0, n_ray = 0;
-    if (t == 0) {
-        for (int i = 0; i < 3; ++i) s_nq[i] = s_dry[i] = 0;
-    }
+    if (lane == 0) s_cnt[wid][0] = s_cnt[wid][1] = 0;
+    bool dry = false;          // uniform over the warp: the selected list is exhausted
     for (int r = 0;; ++r) {
         const int rb = r & 1, wb = rb ^ 1;
-        __syncthreads();   // last round's pushes and s_dry are visible; its reads are done
-        const int nq = min(s_nq[r % 3], (int)blockDim.x);
-        const bool dry = s_dry[r % 3] != 0;
-        if (nq == 0 && dry) {                      // uniform over the block
-            const unsigned sums[6] = {__reduce_add_sync(full, n_prop), __reduce_add_sync(full, n_chain),
-                                      __reduce_add_sync(full, n_exam), __reduce_add_sync(full, n_occ),
-                                      __reduce_add_sync(full, n_comp), __reduce_add_sync(full, n_ray)};
-            unsigned long long* dst[6] = {&cnt->propagated, &cnt->chained, &cnt->examined, &cnt->occupied,
-                                          &cnt->children, &cnt->rays};
-            if (lane < 6 && sums[lane]) atomicAdd(dst[lane], (unsigned long long)sums[lane]);
-            break;
-        }
-        if (t == 0) {
-            s_nq[(r + 2) % 3] = 0;
-            s_dry[(r + 2) % 3] = 0;
-            if (dry) s_dry[(r + 1) % 3] = 1;
-        }
-        bool have = t < nq, task = false;
+        __syncwarp();          // last round's queue writes are visible, its reads are done
+        const int nq = min(s_cnt[wid][rb], 32);
+        __syncwarp();          // every lane has read the count before it is reused
+        if (lane == 0) s_cnt[wid][wb] = 0;
+        __syncwarp();
+        const int qr = rb * blockDim.x + wid * 32 + lane;   // this lane's entry in the read buffer
+        bool have = lane < nq, task = false;
         int h = 0, inst = 0, src = -1, hop = 0;
         double d = 0.0, A = 0.0, B = 0.0, px = 0.0, py = 0.0, cIA = -1.0, cIB = -1.0;
         if (have) {
-            h = q_he[rb * blockDim.x + t]; inst = q_inst[rb * blockDim.x + t]; src = q_src[rb * blockDim.x + t]; hop = q_hop[rb * blockDim.x + t];
+            h = q_he[qr]; inst = q_inst[qr]; src = q_src[qr]; hop = q_hop[qr];
             task = (hop & kHopTask) != 0;
             hop &= ~kHopTask;
-            d = q_d[rb * blockDim.x + t]; A = q_A[rb * blockDim.x + t]; B = q_B[rb * blockDim.x + t]; px = q_px[rb * blockDim.x + t]; py = q_py[rb * blockDim.x + t];
-            cIA = q_IA[rb * blockDim.x + t]; cIB = q_IB[rb * blockDim.x + t];
+            d = q_d[qr]; A = q_A[qr]; B = q_B[qr]; px = q_px[qr]; py = q_py[qr];
+            cIA = q_IA[qr]; cIB = q_IB[qr];
         }
         const unsigned need = __ballot_sync(full, !have);
         if (need && !dry) {
             int base = 0;
             if (lane == 0) base = atomicAdd(&cnt->work_next, __popc(need));
             base = __shfl_sync(full, base, 0);
-            if (base + __popc(need) >= n && lane == 0) s_dry[(r + 1) % 3] = 1;
+            if (base + __popc(need) >= n) dry = true;
             if (!have) {
                 const int idx = base + __popc(need & lt);
                 if (idx < n) {
@@ -751,13 +763,21 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
                 }
             }
         }
-        if (!__any_sync(full, have)) continue;     // this warp idles this round
+        if (!__any_sync(full, have)) {             // nothing queued and nothing left to take
+            const unsigned sums[6] = {__reduce_add_sync(full, n_prop), __reduce_add_sync(full, n_chain),
+                                      __reduce_add_sync(full, n_exam), __reduce_add_sync(full, n_occ),
+                                      __reduce_add_sync(full, n_comp), __reduce_add_sync(full, n_ray)};
+            unsigned long long* dst[6] = {&cnt->propagated, &cnt->chained, &cnt->examined, &cnt->occupied,
+                                          &cnt->children, &cnt->rays};
+            if (lane < 6 && sums[lane]) atomicAdd(dst[lane], (unsigned long long)sums[lane]);
+            break;
+        }
         ChildOut c0, c1;
         int nch = 0, occ = 0, ncomp = 0, nray = 0;
         bool prop = false;
-        const int wo = wb * blockDim.x;
+        const int wo = wb * blockDim.x + wid * 32;  // the warp's region of the write buffer
         const TaskQueue tq{q_d + wo, q_A + wo, q_B + wo, q_px + wo, q_py + wo, q_IA + wo, q_IB + wo,
-                           q_he + wo, q_inst + wo, q_src + wo, q_hop + wo, &s_nq[(r + 1) % 3], (int)blockDim.x};
+                           q_he + wo, q_inst + wo, q_src + wo, q_hop + wo, &s_cnt[wid][wb], 32};
         if (have)
             prop = propagate_window<PROV>(w, cnt, req, inst, src, d, h, A, B, px, py, task, hop, tq, c0, c1, nch,
                                           occ, ncomp, nray, cIA, cIB);
@@ -765,12 +785,13 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
                     (!dry || nq >= tail_cut) && seen_child < room;
         // the continuing child goes to the queue while it has room, every other child to
         // the arena
-        const int qs = warp_reserve(&s_nq[(r + 1) % 3], cont ? 1 : 0);
-        if (cont && qs >= (int)blockDim.x) cont = false;
+        const int qs = warp_reserve(&s_cnt[wid][wb], cont ? 1 : 0);
+        if (cont && qs >= 32) cont = false;
         if (cont) {
-            q_he[wb * blockDim.x + qs] = c0.he; q_inst[wb * blockDim.x + qs] = inst; q_src[wb * blockDim.x + qs] = src; q_hop[wb * blockDim.x + qs] = hop + 1;
-            q_d[wb * blockDim.x + qs] = d; q_A[wb * blockDim.x + qs] = c0.A; q_B[wb * blockDim.x + qs] = c0.B; q_px[wb * blockDim.x + qs] = c0.px; q_py[wb * blockDim.x + qs] = c0.py;
-            q_IA[wb * blockDim.x + qs] = c0.IA; q_IB[wb * blockDim.x + qs] = c0.IB;
+            const int q = wo + qs;
+            q_he[q] = c0.he; q_inst[q] = inst; q_src[q] = src; q_hop[q] = hop + 1;
+            q_d[q] = d; q_A[q] = c0.A; q_B[q] = c0.B; q_px[q] = c0.px; q_py[q] = c0.py;
+            q_IA[q] = c0.IA; q_IB[q] = c0.IB;
         }
         const int nwrite = have ? (cont ? nch - 1 : nch) : 0;
         int fill = -1;
@@ -1700,7 +1721,9 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
             continue;
         }
         if (st == PCH_ERR_CAPACITY && (ws->cnt_host->error & kErrProvFull) && attempt < 4) {
-            st = ensure_plog(ws, std::max<long long>(2LL * ws->plog_cap, (long long)ws->cnt_host->n_plog + 1));
+            int most = 0;
+            for (int r = 0; r < kPlogShards; ++r) most = std::max(most, ws->cnt_host->n_plog_shard[r]);
+            st = ensure_plog(ws, std::max<long long>(2LL * ws->plog_cap, (long long)(most + 1) * kPlogShards * 5 / 4));
             if (st != PCH_OK) return st;
             clear_error();
             continue;
@@ -1733,12 +1756,16 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
 constexpr int kNoPick = 0x7f7f7f7f;          // per-vertex pick before any record matched
 constexpr long long kTraceMaxSteps = 1 << 22;
 
-// Per vertex of instance 0: the first record whose distance is the vertex's final one.
-__global__ void k_prov_pick(const ProvRec* __restrict__ log, int n, const unsigned long long* __restrict__ g, int nv,
-                            int* pick) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+// Per vertex of instance 0: the first record (lowest index over the written part of every
+// shard) whose distance is the vertex's final one.
+__global__ void k_prov_pick(const ProvRec* __restrict__ log, int per, const Counters* __restrict__ cnt,
+                            const unsigned long long* __restrict__ g, int nv, int* pick) {
+    const long long n = (long long)per * kPlogShards;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int shard = (int)(i / per);
+        if (i - (long long)shard * per >= cnt->n_plog_shard[shard]) continue;
         const ProvRec r = log[i];
-        if (r.inst == 0 && r.v >= 0 && r.v < nv && r.db == g[r.v]) atomicMin(pick + r.v, i);
+        if (r.inst == 0 && r.v >= 0 && r.v < nv && r.db == g[r.v]) atomicMin(pick + r.v, (int)i);
     }
 }
 
@@ -1900,7 +1927,7 @@ static pch_status trace_paths(pch_mesh* m, const SrcDev* sd, int n_src, const pc
     Workspace* ws = m->ws;
     cudaStream_t s = (cudaStream_t)o.stream;
     const int nv = m->dm.nv;
-    const int n_rec = std::min(ws->cnt_host->n_plog, ws->plog_cap);
+    const int per = ws->plog_cap / kPlogShards;
     Inst I{};
     PCH_CUDA(cudaMemcpyAsync(&I, ws->w.inst, sizeof(Inst), cudaMemcpyDeviceToHost, s));
     int *dpick = nullptr, *dtg = nullptr, *dn = nullptr;
@@ -1914,7 +1941,7 @@ static pch_status trace_paths(pch_mesh* m, const SrcDev* sd, int n_src, const pc
     if (!e) e = cudaMemsetAsync(dpick, 0x7f, sizeof(int) * (size_t)nv, s);
     if (!e) e = cudaStreamSynchronize(s);   // I (the instance table) is needed by value
     if (!e) {
-        k_prov_pick<<<grid_for(4), 256, 0, s>>>(ws->plog, n_rec, I.g, nv, dpick);
+        k_prov_pick<<<grid_for(4), 256, 0, s>>>(ws->plog, per, ws->w.cnt, I.g, nv, dpick);
         if (n_targets > 0)
             k_trace<<<(n_targets + 127) / 128, 128, 0, s>>>(I, ws->plog, dpick, dtg, n_targets, max_points, dpts, dn);
         e = cudaGetLastError();
@@ -1933,16 +1960,112 @@ static pch_status trace_paths(pch_mesh* m, const SrcDev* sd, int n_src, const pc
     return PCH_OK;
 }
 
+// ====================================================================== Voronoi labels
+// The geodesic Voronoi diagram of a source set (Section 7 names it as the use of the
+// multiple-source field): every vertex is labelled with its nearest source.  After a
+// recording solve, each vertex's final event names the pseudo-source vertex its shortest
+// path bends at last (Section 3: a geodesic bends only at saddle or boundary vertices), or
+// the face-point source itself; following those vertices back (their distances strictly
+// fall along the chain) ends at a source, whose index is the label.
+constexpr int kLabelNone = -1;        // unreachable vertex
+constexpr int kLabelBroken = -2;      // no recorded event with the final distance (never expected)
+
+__global__ void k_voronoi_prep(int* vsrc, int nv) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nv; v += gridDim.x * blockDim.x)
+        if (vsrc[v] == 0x7f7f7f7f) vsrc[v] = -1;
+}
+
+// One thread per vertex: walk the chain of last pseudo-sources up to a source.
+__global__ void k_voronoi(const unsigned long long* __restrict__ g, const ProvRec* __restrict__ log,
+                          const int* __restrict__ pick, const int* __restrict__ vsrc, int nv, int* __restrict__ label) {
+    for (int v0 = blockIdx.x * blockDim.x + threadIdx.x; v0 < nv; v0 += gridDim.x * blockDim.x) {
+        int v = v0, lab = kLabelBroken;
+        if (g[v0] >= 0x7FF0000000000000ull) {
+            label[v0] = kLabelNone;
+            continue;
+        }
+        for (int step = 0; step < nv; ++step) {
+            if (vsrc[v] >= 0) {                 // a vertex source
+                lab = vsrc[v];
+                break;
+            }
+            const int pi = pick[v];
+            if (pi == kNoPick) break;
+            const int src = log[pi].src;
+            if (src < 0) {                      // the face-point source -1 - src
+                lab = -1 - src;
+                break;
+            }
+            if (src >= nv || src == v) break;
+            v = src;
+        }
+        label[v0] = lab;
+    }
+}
+
+__global__ void k_vertex_sources(const SrcDev* __restrict__ srcs, int n, int* vsrc) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        if (srcs[i].kind == 0) atomicMin(vsrc + srcs[i].vertex, srcs[i].label);
+}
+
+static pch_status voronoi(pch_mesh* m, const SrcDev* sd, int n_src, const pch_options* opt, int* labels,
+                          double* out_dist, pch_stats* stats) {
+    pch_options o = opt ? *opt : pch_options{};
+    o.out_on_device = 0;
+    double* outs[1] = {out_dist};
+    pch_status st = solve_instances(&m, 1, sd, n_src, &o, outs, out_dist ? kOutHost : kOutNone, stats, 1);
+    if (st != PCH_OK) return st;
+    Workspace* ws = m->ws;
+    cudaStream_t s = (cudaStream_t)o.stream;
+    const int nv = m->dm.nv;
+    const int per = ws->plog_cap / kPlogShards;
+    Inst I{};
+    PCH_CUDA(cudaMemcpyAsync(&I, ws->w.inst, sizeof(Inst), cudaMemcpyDeviceToHost, s));
+    int *dpick = nullptr, *dvsrc = nullptr, *dlab = nullptr;
+    SrcDev* dsd = nullptr;
+    cudaError_t e = cudaMallocAsync(&dpick, sizeof(int) * (size_t)nv, s);
+    if (!e) e = cudaMallocAsync(&dvsrc, sizeof(int) * (size_t)nv, s);
+    if (!e) e = cudaMallocAsync(&dlab, sizeof(int) * (size_t)nv, s);
+    if (!e) e = cudaMallocAsync(&dsd, sizeof(SrcDev) * (size_t)n_src, s);
+    if (!e) e = cudaMemcpyAsync(dsd, sd, sizeof(SrcDev) * (size_t)n_src, cudaMemcpyHostToDevice, s);
+    if (!e) e = cudaMemsetAsync(dpick, 0x7f, sizeof(int) * (size_t)nv, s);
+    if (!e) e = cudaMemsetAsync(dvsrc, 0x7f, sizeof(int) * (size_t)nv, s);   // 0x7f7f7f7f: no source
+    if (!e) e = cudaStreamSynchronize(s);   // I (the instance table) is needed by value
+    if (!e) {
+        k_vertex_sources<<<(n_src + 127) / 128, 128, 0, s>>>(dsd, n_src, dvsrc);
+        k_prov_pick<<<grid_for(4), 256, 0, s>>>(ws->plog, per, ws->w.cnt, I.g, nv, dpick);
+        // vsrc >= 0 marks a vertex source; the fill value 0x7f7f7f7f is turned into -1 here
+        k_voronoi_prep<<<grid_for(4), 256, 0, s>>>(dvsrc, nv);
+        k_voronoi<<<grid_for(4), 256, 0, s>>>(I.g, ws->plog, dpick, dvsrc, nv, dlab);
+        e = cudaGetLastError();
+    }
+    if (!e) e = cudaMemcpyAsync(labels, dlab, sizeof(int) * (size_t)nv, cudaMemcpyDeviceToHost, s);
+    cudaFreeAsync(dpick, s);
+    cudaFreeAsync(dvsrc, s);
+    cudaFreeAsync(dlab, s);
+    cudaFreeAsync(dsd, s);
+    if (!e) e = cudaStreamSynchronize(s);
+    if (e) return set_error(e == cudaErrorMemoryAllocation ? PCH_ERR_OOM : PCH_ERR_CUDA, "voronoi: %s",
+                            cudaGetErrorString(e));
+    if (stats) stats->kernel_launches += 4;
+    return PCH_OK;
+}
+
 }  // namespace pch
 
 using namespace pch;
 
+static SrcDev src_dev(const pch_source& s, int inst, int label) {
+    SrcDev sd{};
+    sd.inst = inst; sd.kind = s.kind; sd.vertex = s.vertex; sd.face = s.face; sd.label = label;
+    for (int k = 0; k < 3; ++k) sd.bary[k] = s.bary[k];
+    return sd;
+}
+
 extern "C" pch_status pch_solve(pch_mesh* m, const pch_source* src, const pch_options* opt, double* out_dist,
                                 pch_stats* stats) {
     if (!m || !src || !out_dist) return set_error(PCH_ERR_INVALID_ARG, "null argument");
-    SrcDev sd{};
-    sd.inst = 0; sd.kind = src->kind; sd.vertex = src->vertex; sd.face = src->face;
-    for (int k = 0; k < 3; ++k) sd.bary[k] = src->bary[k];
+    SrcDev sd = src_dev(*src, 0, 0);
     double* outs[1] = {out_dist};
     return solve_instances(&m, 1, &sd, 1, opt, outs, (opt && opt->out_on_device) ? kOutDevice : kOutHost, stats);
 }
@@ -1951,11 +2074,7 @@ extern "C" pch_status pch_solve_multi(pch_mesh* m, const pch_source* srcs, int32
                                       double* out_dist, pch_stats* stats) {
     if (!m || !srcs || !out_dist || n_sources <= 0) return set_error(PCH_ERR_INVALID_ARG, "null argument");
     std::vector<SrcDev> sd(n_sources);
-    for (int i = 0; i < n_sources; ++i) {
-        sd[i] = SrcDev{};
-        sd[i].inst = 0; sd[i].kind = srcs[i].kind; sd[i].vertex = srcs[i].vertex; sd[i].face = srcs[i].face;
-        for (int k = 0; k < 3; ++k) sd[i].bary[k] = srcs[i].bary[k];
-    }
+    for (int i = 0; i < n_sources; ++i) sd[i] = src_dev(srcs[i], 0, i);
     double* outs[1] = {out_dist};
     return solve_instances(&m, 1, sd.data(), n_sources, opt, outs, (opt && opt->out_on_device) ? kOutDevice : kOutHost,
                            stats);
@@ -1967,9 +2086,7 @@ extern "C" pch_status pch_solve_batch(pch_mesh* const* meshes, const pch_source*
     std::vector<SrcDev> sd(n_instances);
     for (int i = 0; i < n_instances; ++i) {
         if (!out_dists[i]) return set_error(PCH_ERR_INVALID_ARG, "null output for instance %d", i);
-        sd[i] = SrcDev{};
-        sd[i].inst = i; sd[i].kind = srcs[i].kind; sd[i].vertex = srcs[i].vertex; sd[i].face = srcs[i].face;
-        for (int k = 0; k < 3; ++k) sd[i].bary[k] = srcs[i].bary[k];
+        sd[i] = src_dev(srcs[i], i, 0);
     }
     return solve_instances(meshes, n_instances, sd.data(), n_instances, opt, out_dists,
                            (opt && opt->out_on_device) ? kOutDevice : kOutHost, stats);
@@ -1987,12 +2104,17 @@ extern "C" pch_status pch_trace_paths(pch_mesh* m, const pch_source* srcs, int32
     for (int i = 0; i < n_targets; ++i)
         if (targets[i] < 0 || targets[i] >= m->dm.nv) return set_error(PCH_ERR_INVALID_ARG, "target %d out of range", targets[i]);
     std::vector<SrcDev> sd(n_sources);
-    for (int i = 0; i < n_sources; ++i) {
-        sd[i] = SrcDev{};
-        sd[i].inst = 0; sd[i].kind = srcs[i].kind; sd[i].vertex = srcs[i].vertex; sd[i].face = srcs[i].face;
-        for (int k = 0; k < 3; ++k) sd[i].bary[k] = srcs[i].bary[k];
-    }
+    for (int i = 0; i < n_sources; ++i) sd[i] = src_dev(srcs[i], 0, i);
     return trace_paths(m, sd.data(), n_sources, opt, targets, n_targets, max_points, points, n_points, out_dist, stats);
+}
+
+extern "C" pch_status pch_voronoi(pch_mesh* m, const pch_source* srcs, int32_t n_sources, const pch_options* opt,
+                                  int32_t* labels, double* out_dist, pch_stats* stats) {
+    clear_error();
+    if (!m || !srcs || n_sources <= 0 || !labels) return set_error(PCH_ERR_INVALID_ARG, "null argument or no source");
+    std::vector<SrcDev> sd(n_sources);
+    for (int i = 0; i < n_sources; ++i) sd[i] = src_dev(srcs[i], 0, i);
+    return voronoi(m, sd.data(), n_sources, opt, labels, out_dist, stats);
 }
 
 extern "C" pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float* chosen, int32_t* n_rows) {
@@ -2019,6 +2141,12 @@ extern "C" pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* feat
 #include <sstream>
 #include <string>
 
+#ifndef PCH_BUILD_ID
+#define PCH_BUILD_ID "unversioned"
+#endif
+
+extern "C" const char* pch_build_id(void) { return PCH_BUILD_ID; }
+
 extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_options* opt, const char* cache_path,
                                    double* best_ms) {
     clear_error();
@@ -2030,7 +2158,8 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
     std::string name(prop.name);
     for (auto& ch : name) if (ch == ' ' || ch == '|') ch = '_';
     std::ostringstream keyss;
-    keyss << name << "|nv=" << m->dm.nv << "|nf=" << m->dm.nf << "|control=" << opt->control;
+    keyss << name << "|build=" << PCH_BUILD_ID << "|nv=" << m->dm.nv << "|nf=" << m->dm.nf
+          << "|control=" << opt->control << "|flags=" << opt->flags;
     const std::string key = keyss.str();
     if (cache_path) {
         std::ifstream in(cache_path);
@@ -2050,9 +2179,7 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
             }
         }
     }
-    SrcDev sd{};
-    sd.kind = src->kind; sd.vertex = src->vertex; sd.face = src->face;
-    for (int q = 0; q < 3; ++q) sd.bary[q] = src->bary[q];
+    SrcDev sd = src_dev(*src, 0, 0);
     pch_options trial = *opt;
     trial.out_on_device = 0;
     double best = 1e300;
@@ -2080,9 +2207,16 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
         if (rc == PCH_OK && ms < best) { best = ms; best_k = k; best_b = b; best_h = hp; }
         return rc;
     };
-    // coordinate search: k at (128, 16) from the largest down (stopping once a k is twice as
-    // slow as the best: smaller ones only add iterations), then hops, then the block size
-    pch_status rc = PCH_OK;
+    // the library's defaults first (so the result is never slower than them, up to the
+    // noise of one timing), then a coordinate search: k at (128, 16) from the largest down
+    // (stopping once a k is twice as slow as the best: smaller ones only add iterations),
+    // then hops, then the block size
+    // (under PCH_CONTROL_LEARNED the network picks k every iteration: only hops and the
+    // block size are searched)
+    const bool learned = opt->control == PCH_CONTROL_LEARNED;
+    pch_status rc = consider(default_k(), 64, default_hops());
+    if (rc != PCH_OK) return rc;
+    if (learned) ks.clear();
     for (auto it = ks.rbegin(); it != ks.rend(); ++it) {
         double ms = 0.0;
         if ((rc = time_cfg(*it, 128, 16, ms)) != PCH_OK) return rc;
@@ -2091,7 +2225,7 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
     }
     const long long k_sel = best_k;
     for (int hp : hopss)
-        if (hp != 16 && (rc = consider(k_sel, 128, hp)) != PCH_OK) return rc;
+        if ((learned || hp != 16) && (rc = consider(k_sel, 128, hp)) != PCH_OK) return rc;
     const int h_sel = best_h;
     for (int b : blocks)
         if (b != 128 && (rc = consider(k_sel, b, h_sel)) != PCH_OK) return rc;
@@ -2101,6 +2235,7 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
     if (best_ms) *best_ms = best;
     if (cache_path) {
         std::ofstream out(cache_path, std::ios::app);
+        out.precision(17);
         out << key << " " << best_k << " " << best_b << " " << best_h << " " << best << "\n";
     }
     return PCH_OK;

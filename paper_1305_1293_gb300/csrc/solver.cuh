@@ -6,6 +6,8 @@ namespace pch {
 
 struct SrcDev {
     int inst, kind, vertex, face;
+    int label;              // index of the source in the caller's list (Voronoi labels)
+    int pad;
     double bary[3];
 };
 

@@ -89,8 +89,11 @@ def _load():
         "pch_trace_fetch": (I32, [P, I32, P, P, P]),
         "pch_measure_fp64_peak": (I32, [P]),
         "pch_autotune": (I32, [P, P, P, ctypes.c_char_p, P]),
+        "pch_build_id": (ctypes.c_char_p, []),
         "pch_selftest_math": (I32, [P, I32, P]),
         "pch_trace_paths": (I32, [P, P, I32, P, P, I32, I32, P, P, P, P]),
+        "pch_voronoi": (I32, [P, P, I32, P, P, P, P]),
+        "pch_iso_contours": (I32, [P, P, I32, P, I32, P, I64, P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -240,6 +243,43 @@ def trace_paths(mesh: Mesh, sources, targets, *, face=None, bary=None, max_point
     return (dist, paths, st.as_dict()) if stats else (dist, paths)
 
 
+def voronoi(mesh: Mesh, sources, *, faces=None, barys=None, stats=False, **opts):
+    """Geodesic Voronoi labels (pch_voronoi): index of the nearest of ``sources`` (vertex
+    ids), then of the face points ``faces``/``barys``, for every vertex (-1 unreachable).
+    Returns (labels, dist) or (labels, dist, stats)."""
+    src_list = [make_source(s) for s in (sources or [])]
+    src_list += [make_source(face=f, bary=b) for f, b in zip(faces or [], barys or [])]
+    srcs = (Source * len(src_list))(*src_list)
+    labels = np.empty(mesh.nv, dtype=np.int32)
+    dist = np.empty(mesh.nv, dtype=np.float64)
+    o = make_options(**opts)
+    st = Stats()
+    _check(lib.pch_voronoi(mesh.handle, srcs, len(src_list), ctypes.byref(o), labels.ctypes.data, dist.ctypes.data,
+                           ctypes.byref(st)))
+    return (labels, dist, st.as_dict()) if stats else (labels, dist)
+
+
+CONTOUR_DTYPE = np.dtype([("level", np.int32), ("face", np.int32), ("half_edge", np.int32, 2), ("t", np.float64, 2)])
+
+
+def iso_contours(mesh: Mesh, dist, levels, capacity: int | None = None):
+    """Iso-contour segments (pch_iso_contours) of the field ``dist`` (numpy array, or a
+    torch CUDA tensor) at ``levels``: a structured array with fields level, face,
+    half_edge[2], t[2], ordered by face then level."""
+    lev = np.ascontiguousarray(levels, dtype=np.float64)
+    on_dev = not isinstance(dist, np.ndarray)
+    d = dist if on_dev else np.ascontiguousarray(dist, dtype=np.float64)
+    n = ctypes.c_int64()
+    if capacity is None:
+        _check(lib.pch_iso_contours(mesh.handle, _ptr(d), int(on_dev), lev.ctypes.data, lev.size, None, 0,
+                                    ctypes.byref(n)))
+        capacity = n.value
+    out = np.zeros(max(int(capacity), 1), dtype=CONTOUR_DTYPE)
+    _check(lib.pch_iso_contours(mesh.handle, _ptr(d), int(on_dev), lev.ctypes.data, lev.size, out.ctypes.data,
+                                int(capacity), ctypes.byref(n)))
+    return out[:min(n.value, int(capacity))]
+
+
 def mlp_num_features() -> int:
     return lib.pch_mlp_num_features()
 
@@ -296,6 +336,11 @@ def autotune(mesh: Mesh, source: int, cache_path: str | None = None, **opts):
     _check(lib.pch_autotune(mesh.handle, ctypes.byref(src), ctypes.byref(o),
                             cache_path.encode() if cache_path else None, ctypes.byref(ms)))
     return {"k": int(o.k), "block": int(o.block), "hops": int(o.hops), "ms": ms.value}
+
+
+def build_id() -> str:
+    """SHA-256 prefix of the library's sources (keys the autotuner's cache)."""
+    return lib.pch_build_id().decode()
 
 
 def load_controller(path: str | None = None) -> bool:

@@ -52,6 +52,86 @@ def test_forward_special_cases():
     assert np.allclose(y, [-(2.0 * 1.5) * 3.0 * 0.5, 0.0])
 
 
+def _adam_constant_gradient_error(step, t_max=6):
+    """Largest deviation of ``step`` (an Adam update with the adam_step signature) from
+    the closed form of Kingma & Ba, "Adam: A Method for Stochastic Optimization" (ICLR
+    2015), Algorithm 1, under a constant gradient g.  Then m_t = (1 - b1^t) g and
+    v_t = (1 - b2^t) g^2, so the bias-corrected moments are exactly g and g^2 at every t
+    and each step moves a parameter by lr g / (|g| + eps): after t steps
+    p_0 - t lr g / (|g| + eps).  The gradients include ones of the size of eps, where the
+    step is visibly not lr sign(g) (that pins where eps enters), and zero."""
+    lr, eps = 1e-3, 1e-8
+    g = np.array([1.0, -2.5, 1e3, 1e-8, -3e-9, 0.0, 7e-5])
+    p0 = np.linspace(-1.0, 1.0, g.size)
+    p, m, v = p0.copy(), np.zeros_like(g), np.zeros_like(g)
+    worst = 0.0
+    for t in range(1, t_max + 1):
+        p, m, v = step(p, g, m, v, t, lr)
+        exact = p0 - t * lr * g / (np.abs(g) + eps)
+        worst = max(worst, float(np.max(np.abs(p - exact))) / lr)
+    return worst
+
+
+def _adam_impulse_error(step, t_max=6, b1=0.9, b2=0.999):
+    """Deviation of ``step`` from the closed form of Adam's recurrences for a gradient g at
+    step 1 and zero afterwards: m_t = b1^(t-1) (1 - b1) g and v_t = b2^(t-1) (1 - b2) g^2,
+    so the step t update is lr m_t / (1 - b1^t) / (sqrt(v_t / (1 - b2^t)) + eps).  Unlike
+    the constant gradient this depends on the two decay rates."""
+    lr, eps = 1e-3, 1e-8
+    g = np.array([1.0, -2.5, 1e-8, 0.0])
+    p0 = np.linspace(-1.0, 1.0, g.size)
+    p, m, v = p0.copy(), np.zeros_like(g), np.zeros_like(g)
+    exact = p0.copy()
+    worst = 0.0
+    for t in range(1, t_max + 1):
+        p, m, v = step(p, g if t == 1 else np.zeros_like(g), m, v, t, lr)
+        mt = b1 ** (t - 1) * (1 - b1) * g
+        vt = b2 ** (t - 1) * (1 - b2) * g * g
+        exact = exact - lr * (mt / (1 - b1 ** t)) / (np.sqrt(vt / (1 - b2 ** t)) + eps)
+        worst = max(worst, float(np.max(np.abs(p - exact))) / lr)
+    return worst
+
+
+def test_adam_closed_form_constant_gradient():
+    assert _adam_constant_gradient_error(mo.adam_step) <= 1e-12
+    assert _adam_impulse_error(mo.adam_step) <= 1e-12
+    # first step: lr sign(g) up to eps for |g| >> eps, half of it for |g| = eps
+    p1, _, _ = mo.adam_step(np.zeros(3), np.array([2.0, -1e-8, 1e-8]), np.zeros(3), np.zeros(3), 1, 0.01)
+    assert np.allclose(p1, [-0.01, 0.005, -0.005], rtol=1e-7, atol=0)
+
+
+def test_adam_pin_catches_planted_mistakes():
+    """Plausible mistakes in an Adam step, each planted in a copy of the oracle's update,
+    all fail one of the two closed-form pins above."""
+    def no_bias_correction(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        return p - lr * m / (np.sqrt(v) + eps), m, v
+
+    def betas_swapped(p, g, m, v, t, lr):
+        return mo.adam_step(p, g, m, v, t, lr, b1=0.999, b2=0.9)
+
+    def eps_inside_sqrt(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        return p - lr * (m / (1 - b1 ** t)) / np.sqrt(v / (1 - b2 ** t) + eps), m, v
+
+    def corrected_with_t_minus_1(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+        m = b1 * m + (1 - b1) * g
+        v = b2 * v + (1 - b2) * g * g
+        tt = max(t - 1, 1)
+        return p - lr * (m / (1 - b1 ** tt)) / (np.sqrt(v / (1 - b2 ** tt)) + eps), m, v
+
+    def moment_without_one_minus_beta(p, g, m, v, t, lr, b1=0.9, b2=0.999, eps=1e-8):
+        m = b1 * m + g
+        v = b2 * v + (1 - b2) * g * g
+        return p - lr * (m / (1 - b1 ** t)) / (np.sqrt(v / (1 - b2 ** t)) + eps), m, v
+
+    for bad in (no_bias_correction, betas_swapped, eps_inside_sqrt, corrected_with_t_minus_1,
+                moment_without_one_minus_beta):
+        assert max(_adam_constant_gradient_error(bad), _adam_impulse_error(bad)) > 1e-6, bad.__name__
+
+
 def test_adam_reduces_loss_cpu():
     p = mo.init_params(2)
     X, _ = _data(64, 5)

@@ -300,9 +300,12 @@ def _edge_graph_upper(m, s):
     return dijkstra(g, directed=False, indices=s)
 
 
-def _full_size_checks(pch, oracle_lib, m, s, n_near=64):
+def _full_size_checks(pch, oracle_lib, m, s, n_near=64, fixture=None, **opts):
+    """Invariants on every vertex, then parity: against the stored full field of the
+    oracle on every vertex when a fixture is given, else on the n_near vertices nearest
+    the source (which the oracle finalises early: its keys never decrease)."""
     mesh = pch.Mesh(m.vertices, m.faces)
-    got, st = pch.solve(mesh, s, stats=True)
+    got, st = pch.solve(mesh, s, stats=True, **opts)
     mesh.close()
     assert got[s] == 0.0 and np.all(np.isfinite(got))
     chord = np.linalg.norm(m.vertices - m.vertices[s], axis=1)
@@ -311,7 +314,15 @@ def _full_size_checks(pch, oracle_lib, m, s, n_near=64):
     e = np.concatenate([m.faces[:, [0, 1]], m.faces[:, [1, 2]]])
     le = np.linalg.norm(m.vertices[e[:, 0]] - m.vertices[e[:, 1]], axis=1)
     assert np.all(np.abs(got[e[:, 0]] - got[e[:, 1]]) <= le * (1 + 1e-12) + 1e-14)
-    # sampled outputs: vertices the oracle finalises early (its keys never decrease)
+    if fixture is not None:
+        import make_fullfield as mf
+        ref, src, sha, _ = mf.load(fixture)
+        assert src == s and sha == mf.mesh_sha256(m), "the stored field belongs to another mesh"
+        # stored values carry a relative rounding of at most 2^-37 (about 7e-12)
+        err = max_rel(got, ref)
+        print(f"{fixture}: full-field max relative error {err:.3e} over {m.nv} vertices")
+        assert err < TOL
+        return st
     order = np.argsort(got)
     near = order[1:1 + n_near]
     ref, _ = oracle_lib.geodesic(m.vertices, m.faces, s, targets=near)
@@ -319,15 +330,21 @@ def _full_size_checks(pch, oracle_lib, m, s, n_near=64):
     return st
 
 
-def test_full_terrain_512(pch, oracle_lib):
+BENCH_OPTS = {"k": 393216, "hops": 32, "block": 64}     # the terrain's tuned configuration
+
+
+@pytest.mark.parametrize("opts", [{}, BENCH_OPTS], ids=["defaults", "tuned"])
+def test_full_terrain_512(pch, oracle_lib, opts):
+    """The 512 x 512 terrain, every vertex against the oracle's stored full field."""
     meshes, srcs = mg.workload("terrain", "full")
-    st = _full_size_checks(pch, oracle_lib, meshes[0], int(srcs[0][0]), n_near=2000)
+    st = _full_size_checks(pch, oracle_lib, meshes[0], int(srcs[0][0]), fixture="terrain512_centre", **opts)
     assert st["windows_propagated"] > meshes[0].nf
 
 
 def test_full_torus_sources(pch, oracle_lib):
+    """The 1M-face torus from its first source, every vertex against the stored field."""
     meshes, srcs = mg.workload("torus", "full")
-    _full_size_checks(pch, oracle_lib, meshes[0], int(srcs[0][0]), n_near=1000)
+    _full_size_checks(pch, oracle_lib, meshes[0], int(srcs[0][0]), fixture="torus1250x400_src0")
 
 
 def test_fast_reciprocal_and_sqrt_within_few_ulp(pch):
@@ -366,12 +383,22 @@ def _sampled_batch_checks(pch, oracle_lib, meshes, inst, outs, n_near, n_oracle,
 
 def test_full_batch_256_meshes(pch, oracle_lib):
     """The 256-mesh workload at full size in one batched solve (plain control with the
-    tuned chaining), sampled against the oracle on 16 instances."""
+    tuned chaining): every vertex of the 16 smallest instances against the oracle's full
+    field, invariants on every instance, sampled oracle parity on 16 more."""
     meshes, srcs = mg.workload("batch", "full")
     hs = [pch.Mesh(m.vertices, m.faces) for m in meshes]
     inst = [(i, int(s[0])) for i, s in enumerate(srcs)]
     outs = pch.solve_batch([hs[i] for i, _ in inst], [s for _, s in inst], k=24576, hops=16, block=128)
     _sampled_batch_checks(pch, oracle_lib, meshes, inst, outs, n_near=150, n_oracle=16, upper_every=32)
+    smallest = sorted(range(len(inst)), key=lambda j: meshes[inst[j][0]].nf)[:16]
+    worst = 0.0
+    for j in smallest:
+        mi, s = inst[j]
+        ref, _ = oracle_lib.geodesic(meshes[mi].vertices, meshes[mi].faces, s)
+        worst = max(worst, max_rel(outs[j], ref))
+    print(f"batch: full-field max relative error {worst:.3e} on the 16 smallest instances "
+          f"({min(meshes[inst[j][0]].nf for j in smallest)}-{max(meshes[inst[j][0]].nf for j in smallest)} faces)")
+    assert worst < TOL
     for h in hs:
         h.close()
 
