@@ -1,10 +1,18 @@
-"""Benchmark: exact geodesic solves on the 512 x 512 synthetic terrain (524,288 faces).
+"""Benchmark: exact geodesic distance on the largest synthetic workload of the set, the
+5,242,880-face sphere (icosahedron subdivided 9 times, 5% multi-octave radial noise) with
+32 seeded sources, learned selection controller and autotuned propagation tiles.
 
-One step = one complete solve (selection, propagation, organisation, events, until no
-window is pending) from the centre vertex, mesh resident on the device.  Prints one
-JSON line (rank 0).  `--impl reference` times the sequential CPU oracle instead, on a
-bounded sample of the same workload (the oracle stops once a fixed set of vertices
-nearest the source is final).
+One step = one batched solve (selection, propagation, organisation, events, until no
+window is pending) of a group of 8 of the 32 sources in one launch sequence, with the
+learned controller; the steps cycle through the four groups, so every 4 steps solve the
+whole source set.  The mesh is resident on the device; inputs (33 GB of workspace and
+the 1.5 GB mesh) are far larger than L2, and L2 is flushed between steps anyway.  Beside
+it, on the same GPU and group: plain PCH as the paper runs it (k = 24 * 2^10, one hop per
+iteration, one source at a time), plain PCH with the autotuned fixed k (sequential and
+batched), and the 512 x 512 terrain.  Prints one JSON line (rank 0).
+
+`--impl reference` times the sequential CPU oracle instead, on bounded samples of the same
+workload (the oracle stops once a fixed set of vertices nearest the source is final).
 
 Multi-GPU (torchrun): a single solve does not shard, so every rank runs the same
 workload as an independent replica ("replicas only"); value = total windows
@@ -27,13 +35,26 @@ sys.path.insert(0, ROOT)
 
 METRIC = "solve ms & windows/s vs plain PCH on same GB300 at max rel err ≤1e-9"
 UNIT = "windows/s"
-WORKLOAD = "terrain512: 512x512 height-field grid (263,169 V, 524,288 F), 8 sines + N(0,0.01^2), random diagonals, source = centre vertex, fp64"
-# oracle samples: stop once the n vertices nearest the source are final.  The reference
-# arm times one per step (about 1 s on the GPU machine's host); the bench line's cpu_baseline
-# times one larger sample once (about 10-30 s of CPU work)
-NEAR_SAMPLE = 8000
-NEAR_SAMPLE_BASELINE = 30000
+WORKLOAD = ("large: icosahedron subdivided 9x (2,621,442 V, 5,242,880 F), radius 1 + 0.05 N(p)/max|N| with N a "
+            "5-octave sum of 8 random plane waves, 32 seeded source vertices, fp64 geometry, learned selection "
+            "controller (fp32 3 x 64 MLP) and autotuned propagation tiles; the largest configuration of the set, "
+            "the one the metric is quoted on")
+GROUP = 8                     # sources per batched launch sequence (one bench step)
+TERRAIN = "terrain512: 512x512 height-field grid (263,169 V, 524,288 F), 8 sines + N(0,0.01^2), random diagonals, centre source"
+# oracle samples: stop once the n vertices nearest the source are final
+NEAR_SAMPLE = 6000            # the reference arm, per step (a few seconds on one core)
+NEAR_SAMPLE_BASELINE = 15000  # the bench line's cpu_baseline, per core (about 10-30 s each)
 FP64_PEAK_DERIVED = 152 * 4 * 2.07e9 / 1e12   # SMs x FP64 flops/clk/SM x max clock (TFLOP/s)
+TUNE_CACHE = os.path.join(ROOT, "paper_1305_1293_gb300", "autotune_cache.txt")
+
+
+def _peaks():
+    """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
 
 
 def _dist_env():
@@ -90,37 +111,73 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def _near_targets(m, s, n_near):
+    return np.argsort(np.linalg.norm(m.vertices - m.vertices[s], axis=1))[:n_near].astype(np.int32)
+
+
 def oracle_sample(m, s, n_near: int = NEAR_SAMPLE):
     """Time the CPU oracle on a bounded sample: stop once the n_near nearest vertices
     (by Euclidean distance) are final.  Returns windows/s, seconds, windows."""
     import oracle
-    near = np.argsort(np.linalg.norm(m.vertices - m.vertices[s], axis=1))[:n_near]
+    near = _near_targets(m, s, n_near)
     t = time.perf_counter()
-    _, st = oracle.geodesic(m.vertices, m.faces, s, targets=near.astype(np.int32))
+    _, st = oracle.geodesic(m.vertices, m.faces, s, targets=near)
     dt = time.perf_counter() - t
     return st["propagated"] / dt, dt, st["propagated"]
 
 
-def cpu_pch_sample(k: int = 24576):
-    """The paper's CPU PCH (Section 6: rounds of the k nearest windows, unordered) against
-    the sequential priority-queue oracle on the reduced terrain of the same family (48 x 48,
-    4,608 faces, whole field): the window overhead of unordered rounds, which the GPU path
-    shares, and the CPU rate."""
-    import oracle
+def _oracle_worker(job):
+    """One source of the large workload on one host core (process pool, spawn)."""
+    s, n_near = job
+    sys.path.insert(0, ROOT)
     from paper_1305_1293_gb300 import meshgen as mg
-    meshes, srcs = mg.workload("terrain", "small")
-    m, s = meshes[0], int(srcs[0][0])
+    m = mg.workload("large", "full")[0][0]
+    v, dt, w = oracle_sample(m, s, n_near)
+    return s, dt, w
+
+
+def cpu_baseline_parallel(sources, n_near=NEAR_SAMPLE_BASELINE):
+    """The oracle on the machine's host cores, one source per core (spawned processes, no
+    threading inside a solve), each stopped once its n_near nearest vertices are final."""
+    import multiprocessing as mp
+    cores = os.cpu_count() or 1
+    jobs = [(int(s), n_near) for s in sources[:cores]]
     t = time.perf_counter()
-    ref, st_ich = oracle.geodesic(m.vertices, m.faces, s)
-    t_ich = time.perf_counter() - t
+    with mp.get_context("spawn").Pool(len(jobs)) as pool:
+        res = pool.map(_oracle_worker, jobs)
+    wall = time.perf_counter() - t
+    per = [dt for _, dt, _ in res]
+    wins = sum(w for _, _, w in res)
+    return {"value": wins / max(max(per), 1e-9),
+            "unit": UNIT, "cores": len(jobs), "host_cores": cores, "kind": "oracle",
+            "sample": f"one source per core on the large workload ({len(jobs)} of its 32 sources), each oracle run "
+                      f"stopped once the {n_near} vertices nearest its source are final; value = windows of all "
+                      f"cores / the slowest core's time",
+            "per_source_s_median": statistics.median(per), "per_source_s_max": max(per),
+            "wall_s_with_process_start": wall, "windows_total": wins}
+
+
+def full_field_comparison(pch, mg):
+    """Full-field solve time on one stated instance, oracle (one core) against the GPU:
+    the large workload's family at 4 subdivisions fewer (20,480 faces), first source."""
+    import oracle
+    m = mg.multi_octave_sphere(5, 0.05, seed=mg.SEED_BASE + 5)
+    s = int(mg.pick_sources(m, 1, mg.SEED_BASE + 105)[0])
     t = time.perf_counter()
-    d, st_pch = oracle.cpu_pch(m.vertices, m.faces, s, k)
-    t_pch = time.perf_counter() - t
-    return {"mesh": "terrain 48 x 48 (4,608 F), whole field", "k": k, "cores": 1,
-            "ich_windows": st_ich["propagated"], "cpu_pch_windows": st_pch["propagated"],
-            "window_ratio": st_pch["propagated"] / max(1, st_ich["propagated"]), "rounds": st_pch["rounds"],
-            "ich_s": t_ich, "cpu_pch_s": t_pch, "cpu_pch_windows_per_s": st_pch["propagated"] / max(t_pch, 1e-9),
-            "max_rel_diff": float(np.max(np.abs(d - ref) / np.maximum(ref, 1e-300)))}
+    ref, ost = oracle.geodesic(m.vertices, m.faces, s)
+    t_or = time.perf_counter() - t
+    h = pch.Mesh(m.vertices, m.faces)
+    pch.solve(h, s, control=pch.CONTROL_LEARNED)
+    times = []
+    for _ in range(5):
+        d, st = pch.solve(h, s, stats=True, control=pch.CONTROL_LEARNED)
+        times.append(st["ms_total"])
+    h.close()
+    err = float(np.max(np.abs(d - ref) / np.maximum(ref, 1e-300)))
+    return {"instance": f"multi-octave sphere subdivided 5x ({m.nf} F), source {s}, whole field",
+            "oracle_one_core_ms": 1e3 * t_or, "oracle_windows": ost["propagated"],
+            "gpu_learned_ms_median": statistics.median(times), "gpu_windows": st["windows_propagated"],
+            "max_rel_err": err}
 
 
 def run_reference(args):
@@ -130,18 +187,18 @@ def run_reference(args):
     from paper_1305_1293_gb300 import meshgen as mg
     import oracle
     oracle.build()
-    meshes, srcs = mg.workload("terrain", "full")
-    m, s = meshes[0], int(srcs[0][0])
-    for _ in range(args.warmup):
-        oracle_sample(m, s)
-    vals, times, wins = [], [], []
-    for _ in range(args.steps):
-        v, dt, w = oracle_sample(m, s)
-        vals.append(v)
+    meshes, srcs = mg.workload("large", "full")
+    m, sv = meshes[0], [int(x) for x in srcs[0]]
+    for i in range(args.warmup):
+        oracle_sample(m, sv[i % len(sv)])
+    times, wins = [], []
+    for i in range(args.steps):
+        _, dt, w = oracle_sample(m, sv[i % len(sv)])
         times.append(dt)
         wins.append(w)
     value = sum(wins) / sum(times)
-    sample = f"oracle stops once the {NEAR_SAMPLE} vertices nearest the source are final ({wins[0]} windows per step)"
+    sample = (f"each step one source of the large workload (cycling over its 32 sources), the oracle stopped once "
+              f"the {NEAR_SAMPLE} vertices nearest the source are final (mean {int(np.mean(wins))} windows per step)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -149,6 +206,46 @@ def run_reference(args):
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _timed(stream, fn):
+    import torch
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    r = fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b), r
+
+
+def terrain_extras(pch, mg, stream):
+    """The 512 x 512 terrain from its centre (the earlier headline workload): plain PCH
+    with the autotuned fixed k, the paper's setting, and the learned controller."""
+    import torch
+    meshes, srcs = mg.workload("terrain", "full")
+    m, s = meshes[0], int(srcs[0][0])
+    h = pch.Mesh(m.vertices, m.faces)
+    out = torch.empty(m.nv, dtype=torch.float64, device="cuda")
+    t0 = time.perf_counter()
+    tuned = pch.autotune(h, s, cache_path=TUNE_CACHE)
+    tune_s = time.perf_counter() - t0
+    tk = {"k": tuned["k"], "block": tuned["block"], "hops": tuned["hops"]}
+    res = {}
+    for name, kw in (("plain_tuned", tk), ("learned", {"control": pch.CONTROL_LEARNED, "block": tk["block"],
+                                                       "hops": tk["hops"]}),
+                     ("paper_k24576_1hop", {"k": 24576, "hops": 1})):
+        pch.solve(h, s, out=out, stream=stream, **kw)
+        reps = 10 if name != "paper_k24576_1hop" else 2
+        ms, w = [], 0
+        for _ in range(reps):
+            t, (_, st) = _timed(stream, lambda: pch.solve(h, s, out=out, stats=True, stream=stream, **kw))
+            ms.append(t)
+            w = st["windows_propagated"]
+        res[name] = {"ms_median": statistics.median(ms), "windows": w,
+                     "windows_per_s": w / (statistics.median(ms) / 1e3)}
+    h.close()
+    return {"workload": TERRAIN, "tuned": tk, "tune_s": tune_s, **res}
 
 
 def run_gpu(args):
@@ -165,42 +262,39 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.barrier()
     from paper_1305_1293_gb300 import meshgen as mg, pch
+    if not pch.load_controller():
+        raise RuntimeError("trained controller weights are missing (paper_1305_1293_gb300/controller_weights.npy)")
 
-    meshes, srcs = mg.workload("terrain", "full")
-    m, s = meshes[0], int(srcs[0][0])
-    mesh = pch.Mesh(m.vertices, m.faces)
+    meshes, srcs = mg.workload("large", "full")
+    m = meshes[0]
+    sv = [int(x) for x in srcs[0]]
+    groups = [sv[i:i + GROUP] for i in range(0, len(sv), GROUP)]
+    h = pch.Mesh(m.vertices, m.faces)
     stream = torch.cuda.current_stream()
-    out = torch.empty(m.nv, dtype=torch.float64, device="cuda")
+    outs = [torch.empty(m.nv, dtype=torch.float64, device="cuda") for _ in range(GROUP)]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
-    # plain control with the autotuned fixed k, block and hops (cache keyed by GPU and mesh)
-    if args.k:
-        tuned = {"k": args.k, "block": 0, "hops": args.hops}
-    else:
-        tuned = pch.autotune(mesh, s, cache_path=os.path.join(ROOT, "paper_1305_1293_gb300", "autotune_cache.txt"))
-    sopts = {"k": tuned["k"], "block": tuned["block"], "hops": tuned["hops"],
-             "loop": pch.LOOP_HOST if args.loop == "host" else pch.LOOP_GRAPH}
-    opts = dict(stream=stream, **sopts)
+    # the learned controller picks k each iteration; the tuner picks hops and the block
+    t0 = time.perf_counter()
+    tl = pch.autotune(h, sv[0], cache_path=TUNE_CACHE, control=pch.CONTROL_LEARNED)
+    tune_learned_s = time.perf_counter() - t0
+    lopts = {"control": pch.CONTROL_LEARNED, "hops": tl["hops"], "block": tl["block"]}
 
-    def step():
-        return pch.solve(mesh, s, out=out, stats=True, **opts)[1]
+    def step(i):
+        g = groups[i % len(groups)]
+        return pch.solve_batch([h] * len(g), g, outs=outs[:len(g)], stats=True, stream=stream, **lopts)[1]
 
-    for _ in range(args.warmup):
-        step()
+    for i in range(args.warmup):
+        step(i)
     torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
     per_step, stats = [], []
     with ClockSampler(local) as clk:
         torch.cuda.synchronize()
-        for _ in range(args.steps):
+        for i in range(args.steps):
             flush.fill_(1.0)                       # evict L2 between timed steps
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            st = step()
-            b.record(stream)
-            b.synchronize()
-            per_step.append(a.elapsed_time(b))
+            t, st = _timed(stream, lambda: step(i))
+            per_step.append(t)
             stats.append(st)
         torch.cuda.synchronize()
     total_ms = sum(per_step)
@@ -214,123 +308,159 @@ def run_gpu(args):
         dist.all_reduce(w, op=dist.ReduceOp.SUM)
         wins = float(w.item())
     value = wins / (total_ms / 1e3)
-
-    # parity of the benchmarked field on sampled vertices (oracle early stop)
-    got = out.cpu().numpy()
-
-    # per-phase device time (one profiled solve, events around every phase)
-    _, pst = pch.solve(mesh, s, stats=True, flags=pch.FLAG_PROFILE, **{k: v for k, v in sopts.items() if k != "loop"})
-    ph = pst["ms_phase"]
-    prop_ms = ph["propagate"]
-    prop_launches = pst["iterations"]
-    # the paper's own setting on the same GPU and kernels: k = 24 * 2^10, one hop, chosen
-    # by the histogram threshold, and by the paper's strided approximate selection
-    _, paper_st = pch.solve(mesh, s, stats=True, k=24576, hops=1)
-    _, strided_st = pch.solve(mesh, s, stats=True, k=24576, control=pch.CONTROL_STRIDED)
-    achieved_tf = pst["prop_fp64_ops"] / (prop_ms / 1e3) / 1e12
-    fp64_meas = pch.measure_fp64_peak()
-
-    # end to end through the C ABI with host buffers (mesh upload + solve + download)
-    vh = torch.from_numpy(m.vertices).pin_memory().numpy()
-    fh = torch.from_numpy(m.faces).pin_memory().numpy()
-    res = torch.empty(m.nv, dtype=torch.float64).pin_memory().numpy()
-    e2e_ms, e2e_w = [], 0
-    for i in range(max(1, args.steps // 2)):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        mm = pch.Mesh(vh, fh)
-        _, st = pch.solve(mm, s, out=res, stats=True, **sopts)
-        mm.close()
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        e2e_w += st["windows_propagated"]
-    e2e_value = e2e_w / (sum(e2e_ms) / 1e3)
+    last_group = groups[(args.steps - 1) % len(groups)]
+    got = [o.cpu().numpy() for o in outs[:len(last_group)]]
 
     line = None
     if rank == 0:
+        g0 = groups[0]
+        # ---- plain PCH on the same GPU and group
+        t0 = time.perf_counter()
+        tp = pch.autotune(h, sv[0], cache_path=TUNE_CACHE)
+        tune_plain_s = time.perf_counter() - t0
+        popts = {"k": tp["k"], "hops": tp["hops"], "block": tp["block"]}
+        seq_ms, seq_w = 0.0, 0
+        for s in g0:
+            t, (_, st) = _timed(stream, lambda: pch.solve(h, s, out=outs[0], stats=True, stream=stream, **popts))
+            seq_ms += t
+            seq_w += st["windows_propagated"]
+        t, (_, bst) = _timed(stream, lambda: pch.solve_batch([h] * len(g0), g0, outs=outs[:len(g0)], stats=True,
+                                                             stream=stream, **popts))
+        bat_ms, bat_w = t, bst["windows_propagated"]
+        t, (_, lst) = _timed(stream, lambda: pch.solve_batch([h] * len(g0), g0, outs=outs[:len(g0)], stats=True,
+                                                             stream=stream, **lopts))
+        lrn_g0_ms, lrn_g0_w = t, lst["windows_propagated"]
+        # the paper's setting: measured on the group's first source, counted for the group
+        pch.solve(h, g0[0], out=outs[0], stream=stream, k=24576, hops=1)   # warm its graph
+        t, (_, pst0) = _timed(stream, lambda: pch.solve(h, g0[0], out=outs[0], stats=True, stream=stream,
+                                                         k=24576, hops=1))
+        paper_ms_per_source = t
+        # ---- per-phase device time of one headline step (events around every phase)
+        _, prof = pch.solve_batch([h] * len(g0), g0, stats=True, flags=pch.FLAG_PROFILE, **lopts)
+        ph = prof["ms_phase"]
+        prop_launches = prof["iterations"]
+        achieved_tf = prof["prop_fp64_ops"] / (ph["propagate"] / 1e3) / 1e12
+        fp64_meas = pch.measure_fp64_peak()
+        hbm, hbm_src = _peaks()
+        # ---- end to end through the C ABI with host buffers: mesh upload and build, one
+        # group's batched solve, download of its fields
+        vh = torch.from_numpy(m.vertices).pin_memory().numpy()
+        fh = torch.from_numpy(m.faces).pin_memory().numpy()
+        res = [torch.empty(m.nv, dtype=torch.float64).pin_memory().numpy() for _ in range(GROUP)]
+        e2e_ms, e2e_w = [], 0
+        for i in range(2):
+            g = groups[i % len(groups)]
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            mm = pch.Mesh(vh, fh)
+            _, st = pch.solve_batch([mm] * len(g), g, outs=res[:len(g)], stats=True, **lopts)
+            mm.close()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+            e2e_w += st["windows_propagated"]
+        e2e_value = e2e_w / (sum(e2e_ms) / 1e3)
+        # ---- parity of the benchmarked fields on sampled vertices (oracle early stop)
         import oracle
         oracle.build()
-        near = np.argsort(got)[1:201]
-        ref, _ = oracle.geodesic(m.vertices, m.faces, s, targets=near.astype(np.int32))
-        parity = float(np.max(np.abs(got[near] - ref[near]) / ref[near]))
-        cpu_v, cpu_dt, cpu_w = oracle_sample(m, s, NEAR_SAMPLE_BASELINE)
-        cpu_pch = cpu_pch_sample()
+        parity = 0.0
+        for j in (0, len(last_group) - 1):
+            near = np.argsort(got[j])[1:201].astype(np.int32)
+            ref, _ = oracle.geodesic(m.vertices, m.faces, last_group[j], targets=near)
+            parity = max(parity, float(np.max(np.abs(got[j][near] - ref[near]) / ref[near])))
+        terrain = terrain_extras(pch, mg, stream)
+        cpu = cpu_baseline_parallel(sv)
+        ff = full_field_comparison(pch, mg)
         clocks = clk.summary()
-        st0 = stats[-1]
+        ms_step = total_ms / args.steps
+        paper_group_ms = paper_ms_per_source * len(g0)
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "control": "plain (fixed k)", "k": sopts["k"], "hops": sopts["hops"],
-                       "block": sopts["block"], "loop": args.loop,
+            "config": {"workload": WORKLOAD, "step": f"one batched solve of {GROUP} of the 32 sources (cycling "
+                                                     f"over the 4 groups)",
+                       "control": "learned", "hops": lopts["hops"], "block": lopts["block"],
                        "parallelism": "replicas" if ws > 1 else "single GPU",
                        "l2": "flushed between timed steps (256 MB write); working set > L2",
-                       "windows_per_solve": st0["windows_propagated"], "iterations": st0["iterations"],
-                       "peak_pending": st0["peak_pending"]},
-            "solve_ms": total_ms / args.steps,
-            "paper_setting_solve_ms": paper_st["ms_total"],
-            "paper_setting_windows": paper_st["windows_propagated"],
-            "paper_strided_solve_ms": strided_st["ms_total"],
-            "paper_strided_windows": strided_st["windows_propagated"],
+                       "windows_per_step_mean": int(np.mean([st["windows_propagated"] for st in stats])),
+                       "iterations_per_step_mean": float(np.mean([st["iterations"] for st in stats]))},
+            "solve_ms_per_source": ms_step / GROUP,
+            "solve_ms_all_32_sources": ms_step * len(groups),
+            "vs_plain": {
+                "group": g0, "learned_batched_ms": lrn_g0_ms,
+                "paper_k24576_1hop_sequential_ms": paper_group_ms,
+                "paper_k24576_1hop_note": "measured on the group's first source, times the group size",
+                "tuned_fixed_k_sequential_ms": seq_ms, "tuned_fixed_k_batched_ms": bat_ms, "tuned": popts,
+                "speedup_vs_paper_setting": paper_group_ms / lrn_g0_ms,
+                "speedup_vs_tuned_fixed_k_sequential": seq_ms / lrn_g0_ms,
+                "speedup_vs_tuned_fixed_k_batched": bat_ms / lrn_g0_ms,
+                "windows": {"learned_batched": lrn_g0_w, "tuned_sequential": seq_w, "tuned_batched": bat_w,
+                            "paper_first_source": pst0["windows_propagated"]},
+                "tuner_s": {"learned": tune_learned_s, "plain": tune_plain_s}},
             "parity_max_rel_err_sampled": parity,
             "roofline": {"bound": "alu", "kernel": "k_propagate", "achieved": achieved_tf,
                          "peak": FP64_PEAK_DERIVED, "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_DERIVED,
-                         "traffic": prop_traffic(), "fp64_microbench_tflops": fp64_meas,
-                         "fp64_ops_per_launch": pst["prop_fp64_ops"] / max(1, prop_launches),
-                         "fp64_ops_per_window": pst["prop_fp64_ops"] / max(1, pst["windows_propagated"]),
-                         "launches": prop_launches,
-                         "avg_launch_us": 1e3 * prop_ms / max(1, prop_launches),
-                         "phase_ms": ph, "memory_phases": phase_rooflines(pst, pst["sort_passes"])},
-            "cpu_baseline": {"value": cpu_v, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"sequential oracle on the same terrain, stopped once the "
-                                       f"{NEAR_SAMPLE_BASELINE} nearest vertices are final ({cpu_w} windows, "
-                                       f"{cpu_dt:.1f} s)"},
+                         "peak_note": "152 SMs x 4 FP64 flops/clk x 2.07 GHz (derived)",
+                         "traffic": prop_traffic(prof),
+                         "fp64_microbench_tflops": fp64_meas, "frac_of_measured_dfma": achieved_tf / fp64_meas,
+                         "fp64_ops_per_launch": prof["prop_fp64_ops"] / max(1, prop_launches),
+                         "fp64_ops_per_window": prof["prop_fp64_ops"] / max(1, prof["windows_propagated"]),
+                         "launches": prop_launches, "avg_launch_us": 1e3 * ph["propagate"] / max(1, prop_launches),
+                         "phase_ms": ph, "memory_phases": phase_rooflines(prof, prof["sort_passes"], hbm),
+                         "hbm_peak_gbs": hbm, "hbm_peak_source": hbm_src},
+            "cpu_baseline": cpu,
+            "full_field_small_instance": ff,
             "e2e": {"value": e2e_value, "unit": UNIT, "ms_per_step": sum(e2e_ms) / len(e2e_ms),
                     "h2d_bytes_per_step": int(m.vertices.nbytes + m.faces.nbytes),
-                    "d2h_bytes_per_step": int(8 * m.nv)},
-            "cpu_pch_baseline": cpu_pch,
+                    "d2h_bytes_per_step": int(8 * m.nv * GROUP)},
+            "terrain512": terrain,
             "gpu_launches": int(sum(st["kernel_launches"] for st in stats)),
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
-    mesh.close()
+    h.close()
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
         dist.destroy_process_group()
 
 
-HBM_PEAK_GBS = 6699.8   # measured STREAM-style copy bandwidth of a GB300 (MEASURED_PEAKS.json hbm_gbs)
-
-# DRAM bytes (read + write) per k_propagate launch on this workload, from the ncu launch
-# list in profiles/terrain512_launch_list.md, valid only for the kernel sources it was
-# taken on (their hash); any change of them reports null until the list is taken again.
-PROP_TRAFFIC = {"sources_sha256_16": "0d616c4973624cd2", "bytes_per_launch": 26.80e6}
+# DRAM bytes (read + write) per propagated window of k_propagate, from an ncu capture of
+# mid-solve launches of a smaller batched sphere of the same family (profiles/), valid
+# only for the kernel sources it was taken on (their hash); scaled to a launch of the
+# benchmark by its windows.  Any change of the sources reports null until it is taken again.
+PROP_TRAFFIC = {"sources_sha256_16": None, "bytes_per_window": None}
 PROP_SOURCES = ("paper_1305_1293_gb300/csrc/solver.cu", "paper_1305_1293_gb300/csrc/pch_common.cuh",
                 "paper_1305_1293_gb300/csrc/fastmath.cuh")
 
 
-def prop_traffic():
+def prop_sources_hash():
     import hashlib
     h = hashlib.sha256()
     for f in PROP_SOURCES:
         with open(os.path.join(ROOT, f), "rb") as fh:
             h.update(fh.read())
-    return PROP_TRAFFIC["bytes_per_launch"] if h.hexdigest()[:16] == PROP_TRAFFIC["sources_sha256_16"] else None
+    return h.hexdigest()[:16]
 
 
-def phase_rooflines(pst, passes):
+def prop_traffic(prof):
+    if PROP_TRAFFIC["bytes_per_window"] is None or prop_sources_hash() != PROP_TRAFFIC["sources_sha256_16"]:
+        return None
+    return PROP_TRAFFIC["bytes_per_window"] * prof["windows_examined"] / max(1, prof["iterations"])
+
+
+def phase_rooflines(pst, passes, hbm):
     """Achieved FP64 rate of k_propagate and HBM rates of the memory-bound phases from the
     algorithmic work counted in one profiled solve (bytes per window as in the comments below)."""
     ph = pst["ms_phase"]
     out = {"propagate_fp64_tflops": pst["prop_fp64_ops"] / max(ph["propagate"], 1e-9) / 1e9}
-    sel_bytes = 128 * pst["windows_scanned"]                        # 60 B in + 60 B out + 8 B gather
+    sel_bytes = 160 * pst["windows_scanned"]                        # 76 B in + 76 B out + 8 B gather
     sort_bytes = pst["windows_sorted"] * (8 + 20 * passes)          # pass 0 reads he/inst; 4+8+8 B a pass
-    app_bytes = 240 * pst["windows_sorted"]                         # key/index 8, window 60, record 96, g 16, out 60
+    app_bytes = 276 * pst["windows_sorted"]                         # key/index 8, window 76, record 96, g 16, out 76
     for name, b, ms in (("select", sel_bytes, ph["select"]), ("sort", sort_bytes, ph["sort"]),
                         ("append", app_bytes, ph["append"])):
         gbs = b / max(ms, 1e-9) / 1e6
         out[name + "_gbs"] = gbs
-        out[name + "_hbm_frac"] = gbs / HBM_PEAK_GBS
+        out[name + "_hbm_frac"] = gbs / hbm
     out["propagate_fp64_frac"] = out["propagate_fp64_tflops"] / FP64_PEAK_DERIVED
     return out
 
@@ -378,7 +508,7 @@ def run_workload(args):
     if not big:
         res["plain_paper_k24576_hops1"] = seq(k=24576, hops=1)[:2]
         res["strided_paper_k24576"] = seq(k=24576, control=pch.CONTROL_STRIDED)[:2]
-    tuned = pch.autotune(handles[0], hsrc[0], cache_path=os.path.join(ROOT, "paper_1305_1293_gb300", "autotune_cache.txt"))
+    tuned = pch.autotune(handles[0], hsrc[0], cache_path=TUNE_CACHE)
     tk = {"k": tuned["k"], "block": tuned["block"], "hops": tuned["hops"]}
     if not big:
         res["plain_tuned"] = seq(**tk)[:2]
@@ -401,7 +531,7 @@ def run_workload(args):
         worst = max(worst, float(np.max(np.abs(d[near] - ref[near]) / ref[near])))
     # profiled run of the tuned configuration on the first instance (roofline)
     _, pst = pch.solve(hmesh[0], hsrc[0], stats=True, flags=pch.FLAG_PROFILE, **tk)
-    roof = phase_rooflines(pst, pst["sort_passes"])
+    roof = phase_rooflines(pst, pst["sort_passes"], _peaks()[0])
     best_name = min(res, key=lambda k: res[k][0])
     t, w = res[best_name]
     line = {"workload": args.workload, "metric": METRIC, "value": w / (t / 1e3), "unit": UNIT,
@@ -431,7 +561,7 @@ def run_paths(args):
     meshes, srcs = mg.workload("terrain", "full")
     m, src = meshes[0], int(srcs[0][0])
     h = pch.Mesh(m.vertices, m.faces)
-    tuned = pch.autotune(h, src, cache_path=os.path.join(ROOT, "paper_1305_1293_gb300", "autotune_cache.txt"))
+    tuned = pch.autotune(h, src, cache_path=TUNE_CACHE)
     tk = {"k": tuned["k"], "block": tuned["block"], "hops": tuned["hops"]}
     rng = np.random.default_rng(0xC0FFEE + 1)
     targets = rng.choice(m.nv, size=4096, replace=False).astype(np.int32)
@@ -516,13 +646,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--k", type=int, default=0, help="windows per iteration (0 = autotuned)")
-    ap.add_argument("--hops", type=int, default=0, help="with --k: propagation hops (0 = library default)")
-    ap.add_argument("--workload", default="terrain",
-                    choices=["terrain", "icosphere", "torus", "batch", "multisrc", "large", "paths"],
-                    help="terrain = the benchmark line; others print a per-workload report line")
-    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
-                    help="iteration driver: CUDA graph with device-side termination, or host-driven (for ncu)")
+    ap.add_argument("--workload", default="bench",
+                    choices=["bench", "icosphere", "terrain", "torus", "batch", "multisrc", "large", "paths"],
+                    help="bench = the benchmark line; others print a per-workload report line")
     ap.add_argument("--ncu-case", default=None, choices=sorted(NCU_CASES),
                     help="run one untimed solve of a small case for an ncu capture")
     args = ap.parse_args()
@@ -532,7 +658,7 @@ def main():
         run_reference(args)
     elif args.workload == "paths":
         run_paths(args)
-    elif args.workload != "terrain":
+    elif args.workload != "bench":
         run_workload(args)
     else:
         run_gpu(args)

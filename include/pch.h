@@ -130,6 +130,9 @@ typedef struct {
     int64_t windows_examined;     /* windows the propagation kernel tested (selected + chained) */
     int64_t windows_occupied;     /* of those, windows whose rays reach the opposite vertex */
     int64_t children_computed;    /* child windows whose geometry was computed (before the filter) */
+    int64_t fan_ties;             /* fans made for a tie: a pseudo-source vertex reached at its
+                                     final distance (within the filters' margin) from a second
+                                     direction */
 } pch_stats;
 
 /* Build a mesh: host arrays `vertices` (n_vertices x 3 doubles, xyz) and `faces`

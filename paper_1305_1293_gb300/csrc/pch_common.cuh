@@ -96,7 +96,7 @@ struct Inst {
     unsigned long long* g;      // geod_dist[] as ordered u64 images of nonnegative doubles
     unsigned long long* ang;    // angle_split[]: packed (rounded-up distance, crossing position)
     unsigned* stamp;            // per-vertex iteration stamp (one fan request per iteration)
-    double* fan_phi;            // per-vertex incoming direction of the best event this iteration
+    float* fan_phi;             // per-vertex angular position of the incoming ray of its last primary fan
     int nv, nh;
     long long keybase;          // sort key = keybase + half-edge
     double lbar;
@@ -136,6 +136,7 @@ struct Counters {
     unsigned long long fans, fan_windows, fan_cand, chained;
     unsigned long long examined, occupied, children, rays;   // propagation path counts (FP64 op tally)
     unsigned long long scanned, sorted;               // windows read by compaction / sorted
+    unsigned long long fan_ties;                      // deferred ties fanned (a new direction)
     int work_next;          // next work-list index handed to a propagation lane
     int n_plog;             // unused (kept for the layout); see n_plog_shard
     int n_plog_shard[32];   // provenance records reserved per shard (geodesic paths)
@@ -172,7 +173,7 @@ struct FanReq {
     int inst;
     unsigned v;
     int href;       // half-edge leaving v whose frame holds (dx, dy); -1: every direction
-    int pad;
+    int tie;        // 1: a tie deferred from the previous iteration (fanned if its direction is new)
     double D;       // the event's distance
     double dx, dy;  // from v towards the event's pseudo-source, in href's frame
 };

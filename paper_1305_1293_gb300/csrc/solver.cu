@@ -125,33 +125,37 @@ __device__ __forceinline__ void log_event(const Work& w, const EvSrc& es, unsign
 }
 
 // Distance event (Algorithm 2, Algorithm 4): min into geod_dist.  Returns true when the
-// event lowered the distance of a pseudo-source vertex: the caller then files a fan
-// candidate carrying the event's incoming direction.  With PROV an event that lowered the
-// distance is also recorded with its origin `es` (geodesic paths).
+// event lowered the distance of a pseudo-source vertex, or tied with it (equal within the
+// filters' relative margin): the caller then files a fan candidate carrying the event's
+// incoming direction.  A tie matters where a saddle is reached along two shortest paths
+// from different directions: the region behind it is the union of both directions'
+// fanned areas.  With PROV an event that lowered the distance is also recorded with its
+// origin `es` (geodesic paths).
 template <bool PROV = false>
 __device__ __forceinline__ bool vertex_event(const Inst& I, unsigned vf, double D, double& gcache,
                                              const Work* w = nullptr, const EvSrc* es = nullptr) {
-    if (!lt_s(D, gcache)) return false;
+    const bool pseudo = (vf & kPseudoBit) != 0;
+    if (!lt_s(D, gcache)) return pseudo && dbits(D) <= dbits(gcache) + kDomUlps;
     unsigned v = vf & ~kPseudoBit;
     unsigned long long nb = dbits(D);
     unsigned long long old = atomicMin(I.g + v, nb);
     if (nb < old) {
         if constexpr (PROV) log_event(*w, *es, v, nb);
         gcache = D;
-        return (vf & kPseudoBit) != 0;
+        return pseudo;
     }
     gcache = bitsd(old);
-    return false;
+    return pseudo && nb <= old + kDomUlps;
 }
 
 // A fan candidate carries the incoming ray as a direction (dx, dy), of any length, in
 // the frame of a reference half-edge href leaving v (href < 0: every direction).
 __device__ __forceinline__ void push_fan(FanReq* req, int* n, int cap, int* err, int inst, unsigned v, double D,
-                                         int href, double dx, double dy) {
+                                         int href, double dx, double dy, int tie = 0) {
     int slot = atomicAdd(n, 1);
     if (slot < cap) {
         FanReq r;
-        r.inst = inst; r.v = v; r.href = href; r.pad = 0; r.D = D; r.dx = dx; r.dy = dy;
+        r.inst = inst; r.v = v; r.href = href; r.tie = tie; r.D = D; r.dx = dx; r.dy = dy;
         req[slot] = r;
     } else {
         atomicOr(err, kErrReqFull);
@@ -837,6 +841,15 @@ constexpr float kPiF = 3.14159265358979f;
 constexpr float kFanPickMargin = 1e-4f;   // radians: corners within this of a wedge boundary are computed exactly
 constexpr double kFanWiden = 1e-9;        // interval widening for FP64 rounding, relative to the edge length
 constexpr int kFanLanes = 8;              // lanes per fan candidate (corners handled in turn)
+// Ties: a fan candidate whose distance equals the vertex's final one within the filters'
+// margin but that did not make the iteration's fan (another candidate did) is deferred to
+// the next iteration and fanned there when its incoming direction differs from that of
+// the vertex's last fan by more than kTieAngle; every fanned area is widened by
+// kTieAngle on both sides, so that directions closer than that are covered by the fan
+// already made.  (Widening is sound: a fan window is a real path, only not a shortest one
+// outside the fanned area.)
+constexpr float kTieAngle = 1e-5f;                      // radians
+constexpr double kTieCos = 0.99999999995, kTieSin = 9.999999999833334e-06;   // cos, sin of kTieAngle
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -880,21 +893,30 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
         const unsigned v = rq.v;
         const double D = rq.D;
         const Inst& I = w.inst[rq.inst];
-        int ok = 0;
+        // 1: the iteration's fan of the vertex; 2: a deferred tie, fanned if its direction
+        // is new; 0: superseded, or deferred now
+        int kind = 0;
         if (sl == 0) {
-            // still the vertex's distance (not superseded), and the first fan this iteration
-            ok = dbits(D) == __ldcg(I.g + v) && atomicExch(I.stamp + v, stamp_fan) != stamp_fan;
-            n_fans += ok ? 1u : 0u;
+            const unsigned long long gv = __ldcg(I.g + v), db = dbits(D);
+            if (db == gv && !rq.tie && atomicExch(I.stamp + v, stamp_fan) != stamp_fan) {
+                kind = 1;
+            } else if (db <= gv + kDomUlps) {
+                if (rq.tie) kind = 2;
+                else push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, v, D, rq.href, rq.dx, rq.dy, 1);
+            }
+            n_fans += kind == 1 ? 1u : 0u;
         }
-        if (!__shfl_sync(gmask, ok, lead)) continue;
+        kind = __shfl_sync(gmask, kind, lead);
+        if (!kind) continue;
         const int s = I.vstart[v], e = I.vstart[v + 1];
         const bool boundary = (I.vflag[v] & 1) != 0;
         const bool all = full_fan != 0 || rq.href < 0;
+        if (all && kind == 2) continue;            // a fan of every direction was made already
         // wedges in FP32 angular coordinates, unwrapped (interior ones are tested at
         // shifts of the total angle T): interior [phi + pi, phi + T - pi]; boundary
         // [-inf, phi - pi] and [phi + pi, +inf]
         const float T = I.vtheta[v];
-        double2 za = make_double2(0.0, 0.0), zb = za, tr = make_double2(1.0, 0.0);
+        double2 za = make_double2(0.0, 0.0), zb = za, tr = make_double2(1.0, 0.0), zlo = za, zhi = za;
         int nw = 0;
         float wlo[2] = {0.f, 0.f}, whi[2] = {0.f, 0.f};
         bool lo_open[2] = {false, false}, hi_open[2] = {false, false};
@@ -906,18 +928,36 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
             za = make_double2(-E.x, -E.y);
             tr = I.vtrot[v];
             zb = cmul(za, tr);
+            if (boundary) phi = fminf(fmaxf(phi, 0.f), T);
+            if (kind == 2) {
+                // a tie: fan only if its incoming direction differs from the last fan's
+                const float fp = I.fan_phi[v];
+                float dphi = fabsf(phi - fp);
+                if (!boundary) {
+                    dphi = fmodf(dphi, T);
+                    dphi = fminf(dphi, T - dphi);
+                }
+                if (dphi <= kTieAngle) continue;       // (a NaN, no fan recorded yet, fans)
+                if (sl == 0) atomicAdd(&cnt->fan_ties, 1ull);
+            } else if (sl == 0) {
+                I.fan_phi[v] = phi;
+            }
             if (boundary) {
-                phi = fminf(fmaxf(phi, 0.f), T);
-                if (phi - kPiF > -kFanPickMargin) {
-                    wlo[nw] = -1e30f; whi[nw] = phi - kPiF; lo_open[nw] = true; ++nw;
+                if (phi - kPiF > -kFanPickMargin - kTieAngle) {
+                    wlo[nw] = -1e30f; whi[nw] = phi - kPiF + kTieAngle; lo_open[nw] = true; ++nw;
                 }
-                if (phi + kPiF < T + kFanPickMargin) {
-                    wlo[nw] = phi + kPiF; whi[nw] = 1e30f; hi_open[nw] = true; ++nw;
+                if (phi + kPiF < T + kFanPickMargin + kTieAngle) {
+                    wlo[nw] = phi + kPiF - kTieAngle; whi[nw] = 1e30f; hi_open[nw] = true; ++nw;
                 }
-            } else if (T - 2.f * kPiF > -kFanPickMargin) {
-                wlo[0] = phi + kPiF; whi[0] = phi + T - kPiF; nw = 1;
+            } else if (T - 2.f * kPiF > -kFanPickMargin - 2.f * kTieAngle) {
+                wlo[0] = phi + kPiF - kTieAngle; whi[0] = phi + T - kPiF + kTieAngle; nw = 1;
             }
             if (nw == 0) continue;
+            // the exact boundaries, widened by kTieAngle: a lower boundary turned clockwise,
+            // an upper one counter-clockwise
+            const double2 wm = make_double2(kTieCos, -kTieSin), wp = make_double2(kTieCos, kTieSin);
+            zlo = cmul(za, wm);
+            zhi = cmul(boundary ? za : zb, wp);
         }
         bool deferred = false;
         for (int j0 = s; j0 < e && !deferred; j0 += kFanLanes) {
@@ -928,7 +968,7 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
             HERec Ro;
             if (j < e) {
                 const int hv = I.vlist[j];
-                bool ex0 = false, ex1 = false, zend_b = false;
+                bool ex0 = false, ex1 = false;
                 int shift = 0;
                 if (all) {
                     has = true;
@@ -943,7 +983,6 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                                 shift = sh;
                                 ex0 = !lo_open[k] && lo > c0 - kFanPickMargin;
                                 ex1 = !hi_open[k] && hi < c1 + kFanPickMargin;
-                                zend_b = !boundary;
                             }
                         }
                 }
@@ -959,8 +998,8 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                         else if (shift == -1) t = make_double2(tr.x, -tr.y);
                         else if (shift == -2) t = cmul_conj(make_double2(tr.x, -tr.y), tr);
                         const double2 cr = I.vrot[hv];
-                        if (ex0) s0 = fmax(fan_hit(Ro, cmul_conj(cmul(za, t), cr)) - kFanWiden * Ro.L, 0.0);
-                        if (ex1) s1 = fmin(fan_hit(Ro, cmul_conj(cmul(zend_b ? zb : za, t), cr)) + kFanWiden * Ro.L, Ro.L);
+                        if (ex0) s0 = fmax(fan_hit(Ro, cmul_conj(cmul(zlo, t), cr)) - kFanWiden * Ro.L, 0.0);
+                        if (ex1) s1 = fmin(fan_hit(Ro, cmul_conj(cmul(zhi, t), cr)) + kFanWiden * Ro.L, Ro.L);
                     }
                 }
             }
@@ -975,8 +1014,9 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                 const int sl2 = base + __popc(bal & below);
                 if (win && sl2 < w.arena_cap) w.arena.he[sl2] = -1;
                 if (sl == 0) {
-                    atomicExch(I.stamp + v, 0u);
-                    push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, v, D, rq.href, rq.dx, rq.dy);
+                    if (kind == 1) atomicExch(I.stamp + v, 0u);
+                    push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, v, D, rq.href, rq.dx, rq.dy,
+                             rq.tie);
                 }
                 deferred = true;
                 continue;
@@ -1159,6 +1199,7 @@ struct Workspace {
     unsigned long long* g_all = nullptr;
     unsigned long long* ang_all = nullptr;
     unsigned* stamp_all = nullptr;
+    float* fanphi_all = nullptr;
     Counters* cnt_host = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // graph cache: rebuilt when pointers or launch parameters change
@@ -1311,6 +1352,7 @@ static pch_status ensure_instances(Workspace* ws, int n_inst, long long g_total,
     if (!e) e = ws->inst_mem.get(&ws->g_all, gc);
     if (!e) e = ws->inst_mem.get(&ws->ang_all, ac);
     if (!e) e = ws->inst_mem.get(&ws->stamp_all, gc);
+    if (!e) e = ws->inst_mem.get(&ws->fanphi_all, gc);
     if (!e) e = ws->inst_mem.get(&w.inst, ic);
     if (!e) e = ws->inst_mem.get(&w.ctl, ic);
     if (!e) e = ws->inst_mem.get(&w.hist[0], (size_t)ic * kBins);
@@ -1506,6 +1548,7 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         stats->windows_examined = (int64_t)c.examined;
         stats->windows_occupied = (int64_t)c.occupied;
         stats->children_computed = (int64_t)c.children;
+        stats->fan_ties = (int64_t)c.fan_ties;
         // algorithmic FP64 operations of k_propagate (add, sub, mul, div, sqrt = 1; fma = 2),
         // counted per code path of propagate_window: a window taken from the work list 7
         // (2 offsets, 5 for the endpoint filter), a chained window 2 (its filter was its
@@ -1638,7 +1681,7 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
         I.g = ws->g_all + gofs[i];
         I.ang = ws->ang_all + aofs[i];
         I.stamp = ws->stamp_all + gofs[i];
-        I.fan_phi = nullptr;
+        I.fan_phi = ws->fanphi_all + gofs[i];
         I.nv = dm.nv; I.nh = dm.nh;
         I.keybase = kbase;
         kbase += dm.nh;
@@ -1702,6 +1745,7 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
         PCH_CUDA(cudaMemsetAsync(w.hist[1], 0, sizeof(unsigned) * kBins * n_inst, s));
         PCH_CUDA(cudaMemsetAsync(ws->ang_all, 0xff, sizeof(unsigned long long) * aoff, s));
         PCH_CUDA(cudaMemsetAsync(ws->stamp_all, 0, sizeof(unsigned) * goff, s));
+        PCH_CUDA(cudaMemsetAsync(ws->fanphi_all, 0xff, sizeof(float) * goff, s));   // NaN: no fan yet
         if (w.trace_rows) PCH_CUDA(cudaMemsetAsync(w.trace_rows, 0, sizeof(int), s));
         if (stats) std::memset(stats, 0, sizeof(pch_stats));
         k_fill_inf<<<grid_for(4), 256, 0, s>>>(ws->g_all, goff);

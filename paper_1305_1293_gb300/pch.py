@@ -58,7 +58,7 @@ class Stats(ctypes.Structure):
                 ("prop_fp64_ops", ctypes.c_int64), ("windows_scanned", ctypes.c_int64),
                 ("windows_sorted", ctypes.c_int64), ("sort_passes", ctypes.c_int64),
                 ("windows_examined", ctypes.c_int64), ("windows_occupied", ctypes.c_int64),
-                ("children_computed", ctypes.c_int64)]
+                ("children_computed", ctypes.c_int64), ("fan_ties", ctypes.c_int64)]
 
     def as_dict(self):
         d = {f[0]: getattr(self, f[0]) for f in self._fields_ if f[0] != "ms_phase"}

@@ -35,7 +35,8 @@ def test_every_declared_symbol_is_exported(pch):
 def test_struct_sizes_match_header(pch):
     assert ctypes.sizeof(pch.Source) == 40
     assert ctypes.sizeof(pch.Options) == 48
-    assert ctypes.sizeof(pch.Stats) == 200
+    assert ctypes.sizeof(pch.Stats) == 208
+    assert pch.CONTOUR_DTYPE.itemsize == 32             # pch_contour_segment: 4 int32 + 2 double
 
 
 def test_mlp_shape(pch):

@@ -99,3 +99,38 @@ def test_library_matches_golden(path):
     fin = np.isfinite(d)
     assert np.array_equal(np.isfinite(got), fin)
     assert float(np.max(np.abs(got - d) / np.maximum(d, 1e-300))) <= 1e-9
+
+
+# ------------------------------------------------------------------ full-size fixtures
+FULL = ["terrain512_centre", "torus1250x400_src0"]
+
+
+@pytest.mark.parametrize("name", FULL)
+def test_full_field_fixture(oracle_lib, name):
+    """The stored full fields of the full-size terrain and torus (written by
+    make_fullfield.py from the oracle): they belong to the generator's current mesh, have
+    the properties of an exact geodesic field on every vertex and edge, and the oracle
+    reproduces them on the vertices nearest the source (an early-stopped run)."""
+    import make_fullfield as mf
+    from paper_1305_1293_gb300 import meshgen as mg
+    assert os.path.exists(mf.path_of(name)), f"{name}.npz missing: run tests/golden/make_fullfield.py"
+    d, s, fsha, probe, wl = mf.load(name)
+    m = mg.workload(wl, "full")[0][0]
+    assert mf.same_mesh(m, fsha, probe)
+    v, f = m.vertices, m.faces
+    assert d.shape == (m.nv,) and d[s] == 0.0 and np.all(np.isfinite(d))
+    q = 2.0 ** -37                       # relative rounding of the stored values
+    chord = np.linalg.norm(v - v[s], axis=1)
+    assert np.all(d >= chord * (1 - 1e-12 - q))
+    e = np.concatenate([f[:, [0, 1]], f[:, [1, 2]], f[:, [2, 0]]])
+    le = np.linalg.norm(v[e[:, 0]] - v[e[:, 1]], axis=1)
+    # each end carries its own rounding: up to 2 q of the larger distance on the difference
+    assert np.all(np.abs(d[e[:, 0]] - d[e[:, 1]]) <= le * (1 + 1e-12) + 2 * q * np.maximum(d[e[:, 0]], d[e[:, 1]]))
+    from scipy.sparse import coo_matrix
+    from scipy.sparse.csgraph import dijkstra as sp_dijkstra
+    g = coo_matrix((le, (e[:, 0], e[:, 1])), shape=(m.nv, m.nv)).tocsr()
+    assert np.all(d <= sp_dijkstra(g, directed=False, indices=s) * (1 + 1e-12 + q))
+    near = np.argsort(chord)[:3000].astype(np.int32)
+    ref, _ = oracle_lib.geodesic(v, f, s, targets=near)
+    r = np.abs(d[near] - ref[near]) / np.maximum(ref[near], 1e-300)
+    assert float(r.max()) <= 1e-11

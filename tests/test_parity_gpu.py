@@ -316,8 +316,8 @@ def _full_size_checks(pch, oracle_lib, m, s, n_near=64, fixture=None, **opts):
     assert np.all(np.abs(got[e[:, 0]] - got[e[:, 1]]) <= le * (1 + 1e-12) + 1e-14)
     if fixture is not None:
         import make_fullfield as mf
-        ref, src, sha, _ = mf.load(fixture)
-        assert src == s and sha == mf.mesh_sha256(m), "the stored field belongs to another mesh"
+        ref, src, fsha, probe, _ = mf.load(fixture)
+        assert src == s and mf.same_mesh(m, fsha, probe), "the stored field belongs to another mesh"
         # stored values carry a relative rounding of at most 2^-37 (about 7e-12)
         err = max_rel(got, ref)
         print(f"{fixture}: full-field max relative error {err:.3e} over {m.nv} vertices")
