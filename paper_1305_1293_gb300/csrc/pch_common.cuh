@@ -96,7 +96,8 @@ struct Inst {
     unsigned long long* g;      // geod_dist[] as ordered u64 images of nonnegative doubles
     unsigned long long* ang;    // angle_split[]: packed (rounded-up distance, crossing position)
     unsigned* stamp;            // per-vertex iteration stamp (one fan request per iteration)
-    float* fan_phi;             // per-vertex angular position of the incoming ray of its last primary fan
+    float* fan_phi;             // per-vertex angular position of the incoming ray of its last fan
+    double2* fan_dir;           // per-vertex unit incoming direction of its last fan (angular frame)
     int nv, nh;
     long long keybase;          // sort key = keybase + half-edge
     double lbar;

@@ -844,12 +844,13 @@ constexpr int kFanLanes = 8;              // lanes per fan candidate (corners ha
 // Ties: a fan candidate whose distance equals the vertex's final one within the filters'
 // margin but that did not make the iteration's fan (another candidate did) is deferred to
 // the next iteration and fanned there when its incoming direction differs from that of
-// the vertex's last fan by more than kTieAngle; every fanned area is widened by
-// kTieAngle on both sides, so that directions closer than that are covered by the fan
-// already made.  (Widening is sound: a fan window is a real path, only not a shortest one
-// outside the fanned area.)
-constexpr float kTieAngle = 1e-5f;                      // radians
-constexpr double kTieCos = 0.99999999995, kTieSin = 9.999999999833334e-06;   // cos, sin of kTieAngle
+// the vertex's last fan: on another sheet of the angular coordinate (more than
+// kTieSheet apart in FP32) or, on the same sheet, by more than kTieDir radians (FP64 unit
+// directions; below that the fanned areas differ by less than the fan intervals'
+// widening kFanWiden).  Events of one geodesic family that tie (the same pseudo-source
+// reached through different windows) are thus fanned once.
+constexpr float kTieSheet = 1e-3f;        // radians
+constexpr double kTieDir = 1e-9;          // radians
 
 __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
     return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
@@ -929,6 +930,8 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
             tr = I.vtrot[v];
             zb = cmul(za, tr);
             if (boundary) phi = fminf(fmaxf(phi, 0.f), T);
+            const double en_s = rsqrt(fma(E.x, E.x, E.y * E.y));
+            const double2 en = make_double2(E.x * en_s, E.y * en_s);   // unit incoming direction
             if (kind == 2) {
                 // a tie: fan only if its incoming direction differs from the last fan's
                 const float fp = I.fan_phi[v];
@@ -937,27 +940,28 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                     dphi = fmodf(dphi, T);
                     dphi = fminf(dphi, T - dphi);
                 }
-                if (dphi <= kTieAngle) continue;       // (a NaN, no fan recorded yet, fans)
+                if (dphi < kTieSheet) {                // (a NaN, no fan recorded yet, fans)
+                    const double2 fd = I.fan_dir[v];
+                    if (fma(en.x, fd.x, en.y * fd.y) > 0.0 && fabs(fma(en.x, fd.y, -en.y * fd.x)) <= kTieDir) continue;
+                }
                 if (sl == 0) atomicAdd(&cnt->fan_ties, 1ull);
             } else if (sl == 0) {
                 I.fan_phi[v] = phi;
+                I.fan_dir[v] = en;
             }
             if (boundary) {
-                if (phi - kPiF > -kFanPickMargin - kTieAngle) {
-                    wlo[nw] = -1e30f; whi[nw] = phi - kPiF + kTieAngle; lo_open[nw] = true; ++nw;
+                if (phi - kPiF > -kFanPickMargin) {
+                    wlo[nw] = -1e30f; whi[nw] = phi - kPiF; lo_open[nw] = true; ++nw;
                 }
-                if (phi + kPiF < T + kFanPickMargin + kTieAngle) {
-                    wlo[nw] = phi + kPiF - kTieAngle; whi[nw] = 1e30f; hi_open[nw] = true; ++nw;
+                if (phi + kPiF < T + kFanPickMargin) {
+                    wlo[nw] = phi + kPiF; whi[nw] = 1e30f; hi_open[nw] = true; ++nw;
                 }
-            } else if (T - 2.f * kPiF > -kFanPickMargin - 2.f * kTieAngle) {
-                wlo[0] = phi + kPiF - kTieAngle; whi[0] = phi + T - kPiF + kTieAngle; nw = 1;
+            } else if (T - 2.f * kPiF > -kFanPickMargin) {
+                wlo[0] = phi + kPiF; whi[0] = phi + T - kPiF; nw = 1;
             }
             if (nw == 0) continue;
-            // the exact boundaries, widened by kTieAngle: a lower boundary turned clockwise,
-            // an upper one counter-clockwise
-            const double2 wm = make_double2(kTieCos, -kTieSin), wp = make_double2(kTieCos, kTieSin);
-            zlo = cmul(za, wm);
-            zhi = cmul(boundary ? za : zb, wp);
+            zlo = za;
+            zhi = boundary ? za : zb;
         }
         bool deferred = false;
         for (int j0 = s; j0 < e && !deferred; j0 += kFanLanes) {
@@ -1200,6 +1204,7 @@ struct Workspace {
     unsigned long long* ang_all = nullptr;
     unsigned* stamp_all = nullptr;
     float* fanphi_all = nullptr;
+    double2* fandir_all = nullptr;
     Counters* cnt_host = nullptr;
     cudaEvent_t ev[2] = {nullptr, nullptr};
     // graph cache: rebuilt when pointers or launch parameters change
@@ -1353,6 +1358,7 @@ static pch_status ensure_instances(Workspace* ws, int n_inst, long long g_total,
     if (!e) e = ws->inst_mem.get(&ws->ang_all, ac);
     if (!e) e = ws->inst_mem.get(&ws->stamp_all, gc);
     if (!e) e = ws->inst_mem.get(&ws->fanphi_all, gc);
+    if (!e) e = ws->inst_mem.get(&ws->fandir_all, gc);
     if (!e) e = ws->inst_mem.get(&w.inst, ic);
     if (!e) e = ws->inst_mem.get(&w.ctl, ic);
     if (!e) e = ws->inst_mem.get(&w.hist[0], (size_t)ic * kBins);
@@ -1682,6 +1688,7 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
         I.ang = ws->ang_all + aofs[i];
         I.stamp = ws->stamp_all + gofs[i];
         I.fan_phi = ws->fanphi_all + gofs[i];
+        I.fan_dir = ws->fandir_all + gofs[i];
         I.nv = dm.nv; I.nh = dm.nh;
         I.keybase = kbase;
         kbase += dm.nh;

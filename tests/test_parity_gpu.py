@@ -364,21 +364,26 @@ def _sampled_batch_checks(pch, oracle_lib, meshes, inst, outs, n_near, n_oracle,
     (1e-9 relative: the bound the workload sets for every distance), and the oracle on
     the n_near vertices nearest the source of n_oracle instances spread over the batch."""
     step = max(1, len(inst) // max(1, n_oracle))
+    worst_chord = worst_lip = 0.0
     for j, ((mi, s), got) in enumerate(zip(inst, outs)):
         m = meshes[mi]
         assert got[s] == 0.0 and np.all(np.isfinite(got)), (j, int(np.sum(~np.isfinite(got))))
         chord = np.linalg.norm(m.vertices - m.vertices[s], axis=1)
         assert np.all(got >= chord * (1 - TOL)), (j, float(np.min(got / np.maximum(chord, 1e-300))))
+        worst_chord = max(worst_chord, float(np.max(1.0 - got[chord > 0] / chord[chord > 0])))
         e = np.concatenate([m.faces[:, [0, 1]], m.faces[:, [1, 2]]])
         le = np.linalg.norm(m.vertices[e[:, 0]] - m.vertices[e[:, 1]], axis=1)
         ratio = np.abs(got[e[:, 0]] - got[e[:, 1]]) / le
         assert np.all(ratio <= 1 + TOL), (j, float(np.max(ratio)))
+        worst_lip = max(worst_lip, float(np.max(ratio)) - 1.0)
         if upper_every and j % upper_every == 0:
             assert np.all(got <= _edge_graph_upper(m, s) * (1 + TOL))
         if j % step == 0:
             near = np.argsort(got)[1:1 + n_near].astype(np.int32)
             ref, _ = oracle_lib.geodesic(m.vertices, m.faces, s, targets=near)
             assert max_rel(got[near], ref[near]) < TOL, (j, s)
+    print(f"{len(inst)} instances: largest chord excess {worst_chord:.2e}, largest edge Lipschitz excess "
+          f"{worst_lip:.2e} (relative)")
 
 
 def test_full_batch_256_meshes(pch, oracle_lib):
