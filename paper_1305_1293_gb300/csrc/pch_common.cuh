@@ -174,7 +174,7 @@ struct FanReq {
     int inst;
     unsigned v;
     int href;       // half-edge leaving v whose frame holds (dx, dy); -1: every direction
-    int tie;        // 1: a tie deferred from the previous iteration (fanned if its direction is new)
+    int tie;        // kind of candidate: from a lowering event, from a tying event, a deferred tie
     double D;       // the event's distance
     double dx, dy;  // from v towards the event's pseudo-source, in href's frame
 };

@@ -131,27 +131,32 @@ __device__ __forceinline__ void log_event(const Work& w, const EvSrc& es, unsign
 // from different directions: the region behind it is the union of both directions'
 // fanned areas.  With PROV an event that lowered the distance is also recorded with its
 // origin `es` (geodesic paths).
+// Return values, also the kinds of fan candidates (FanReq.tie): kEvNone; kReqLowered (the
+// event lowered the distance: a candidate for this iteration's fan of the vertex);
+// kReqTie (it tied with the distance: a candidate compared, an iteration later, with the
+// direction of the vertex's fan); kReqDeferredTie is a tie so deferred.
+enum : int { kEvNone = 0, kReqLowered = 1, kReqTie = 2, kReqDeferredTie = 3 };
 template <bool PROV = false>
-__device__ __forceinline__ bool vertex_event(const Inst& I, unsigned vf, double D, double& gcache,
-                                             const Work* w = nullptr, const EvSrc* es = nullptr) {
+__device__ __forceinline__ int vertex_event(const Inst& I, unsigned vf, double D, double& gcache,
+                                            const Work* w = nullptr, const EvSrc* es = nullptr) {
     const bool pseudo = (vf & kPseudoBit) != 0;
-    if (!lt_s(D, gcache)) return pseudo && dbits(D) <= dbits(gcache) + kDomUlps;
+    if (!lt_s(D, gcache)) return pseudo && dbits(D) <= dbits(gcache) + kDomUlps ? kReqTie : kEvNone;
     unsigned v = vf & ~kPseudoBit;
     unsigned long long nb = dbits(D);
     unsigned long long old = atomicMin(I.g + v, nb);
     if (nb < old) {
         if constexpr (PROV) log_event(*w, *es, v, nb);
         gcache = D;
-        return pseudo;
+        return pseudo ? kReqLowered : kEvNone;
     }
     gcache = bitsd(old);
-    return pseudo && nb <= old + kDomUlps;
+    return pseudo && nb <= old + kDomUlps ? kReqTie : kEvNone;
 }
 
 // A fan candidate carries the incoming ray as a direction (dx, dy), of any length, in
 // the frame of a reference half-edge href leaving v (href < 0: every direction).
 __device__ __forceinline__ void push_fan(FanReq* req, int* n, int cap, int* err, int inst, unsigned v, double D,
-                                         int href, double dx, double dy, int tie = 0) {
+                                         int href, double dx, double dy, int tie = kReqLowered) {
     int slot = atomicAdd(n, 1);
     if (slot < cap) {
         FanReq r;
@@ -278,9 +283,9 @@ __global__ void k_init_face_sources(Work w, const SrcDev* __restrict__ srcs, int
             double dstart = sqrt(x * x + y * y);
             double gc = ldg_dist(I.g, R.v0 & ~kPseudoBit);
             const EvSrc es{s.inst, h, -1 - s.label, 2, x, y};
-            if (w.plog ? vertex_event<true>(I, R.v0, dstart, gc, &w, &es) : vertex_event(I, R.v0, dstart, gc)) {
+            if (const int ev = w.plog ? vertex_event<true>(I, R.v0, dstart, gc, &w, &es) : vertex_event(I, R.v0, dstart, gc)) {
                 // incoming direction: from the corner towards the point, inside face(h)
-                push_fan(w.req[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, R.v0 & ~kPseudoBit, dstart, h, x, y);
+                push_fan(w.req[0], &cnt->n_req, w.req_cap, &cnt->error, s.inst, R.v0 & ~kPseudoBit, dstart, h, x, y, ev);
             }
             if (R.twin < 0) continue;
             // window on twin(h) = (v1 -> v0): point at (L - x, -y), interval [0, L]
@@ -555,14 +560,14 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
             // Algorithm 2: endpoint events at v0 (A = v0) and v1 (B = v1)
             if (le_s(A, tol)) {
                 double D0 = d + (sbits(A) == 0 ? IA : sqrt_nr(fma(px, px, py2)));
-                if (vertex_event<PROV>(I, R.v0, D0, g0, &w, &es))   // the ray arrives at v0 from I (h's frame)
-                    push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v0 & ~kPseudoBit, D0, h, px, py);
+                if (const int ev = vertex_event<PROV>(I, R.v0, D0, g0, &w, &es))   // the ray arrives at v0 from I (h's frame)
+                    push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v0 & ~kPseudoBit, D0, h, px, py, ev);
             }
             if (sbits(L) - sbits(B) <= kSnapUlps) {
                 double q = L - px;
                 double D1 = d + (sbits(B) == sbits(L) ? IB : sqrt_nr(fma(q, q, py2)));
-                if (vertex_event<PROV>(I, R.v1, D1, g1, &w, &es))   // at v1, in the frame of twin(h) = (v1 -> v0)
-                    push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v1 & ~kPseudoBit, D1, R.twin, q, -py);
+                if (const int ev = vertex_event<PROV>(I, R.v1, D1, g1, &w, &es))   // at v1, in the frame of twin(h) = (v1 -> v0)
+                    push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v1 & ~kPseudoBit, D1, R.twin, q, -py, ev);
             }
             // occupancy of v2: the ray I -> v2 crosses e at xs = px + num / den;
             // decided without the division (den > 0), by the signs of fused residuals
@@ -596,13 +601,13 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                     right = angle_pos(xq - kSplitTol) > q;
                     if (!left && !right) left = right = true;
                 }
-                if (vertex_event<PROV>(I, R.v2, D2, g2, &w, &es)) {
+                if (const int ev = vertex_event<PROV>(I, R.v2, D2, g2, &w, &es)) {
                     // the ray arrives at v2 inside face(h); direction to I in the frame of
                     // prev(h) = (v2 -> v0), whose axis is (-xc, -yc) / L2
                     const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
                     const double ux = -xc * R.iL2, uy = -yc * R.iL2, ex = px - xc, ey = py - yc;
                     push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v2 & ~kPseudoBit, D2, hp,
-                             ex * ux + ey * uy, ux * ey - uy * ex);
+                             ex * ux + ey * uy, ux * ey - uy * ex, ev);
                 }
                 if (le_s(B - xcl, tiny)) right = false;
                 if (le_s(xcl - A, tiny)) left = false;
@@ -894,16 +899,20 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
         const unsigned v = rq.v;
         const double D = rq.D;
         const Inst& I = w.inst[rq.inst];
-        // 1: the iteration's fan of the vertex; 2: a deferred tie, fanned if its direction
-        // is new; 0: superseded, or deferred now
+        // 1: the iteration's fan of the vertex (a candidate from an event that lowered its
+        // distance, carrying its final distance, the first this iteration); 2: a tie
+        // deferred an iteration, fanned if its direction is new; 0: superseded, or
+        // deferred now (a tie, or a candidate that did not make the fan but carries the
+        // final distance within the margin)
         int kind = 0;
         if (sl == 0) {
             const unsigned long long gv = __ldcg(I.g + v), db = dbits(D);
-            if (db == gv && !rq.tie && atomicExch(I.stamp + v, stamp_fan) != stamp_fan) {
+            if (rq.tie == kReqLowered && db == gv && atomicExch(I.stamp + v, stamp_fan) != stamp_fan) {
                 kind = 1;
             } else if (db <= gv + kDomUlps) {
-                if (rq.tie) kind = 2;
-                else push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, v, D, rq.href, rq.dx, rq.dy, 1);
+                if (rq.tie == kReqDeferredTie) kind = 2;
+                else push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, v, D, rq.href, rq.dx, rq.dy,
+                              kReqDeferredTie);
             }
             n_fans += kind == 1 ? 1u : 0u;
         }
@@ -1033,11 +1042,13 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                 double ga = ldg_dist(I.g, a), gb = ldg_dist(I.g, b);
                 const EvSrc es{rq.inst, o, (int)v, 1, 0.0, 0.0};   // along the edge from v (PROV only)
                 // incoming directions: at a towards v, in o's frame; at b along next(o) = (b -> v)
-                if (s0 <= 0.0 && vertex_event<PROV>(I, Ro.v0, D + Ro.L2, ga, &w, &es))
-                    push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, a, D + Ro.L2, o, Ro.xc, Ro.yc);
-                if (s1 >= Lo && vertex_event<PROV>(I, Ro.v1, D + Ro.L1, gb, &w, &es))
-                    push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, b, D + Ro.L1, he_next(o), 1.0,
-                             0.0);
+                if (s0 <= 0.0)
+                    if (const int ev = vertex_event<PROV>(I, Ro.v0, D + Ro.L2, ga, &w, &es))
+                        push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, a, D + Ro.L2, o, Ro.xc, Ro.yc, ev);
+                if (s1 >= Lo)
+                    if (const int ev = vertex_event<PROV>(I, Ro.v1, D + Ro.L1, gb, &w, &es))
+                        push_fan(req_nx, &cnt->n_req_next, w.req_cap, &cnt->error, rq.inst, b, D + Ro.L1, he_next(o), 1.0,
+                                 0.0, ev);
                 continue;
             }
             // window on twin(o) = (b -> a): I = v at (Lo - xc, -yc), interval [Lo - s1, Lo - s0]
