@@ -939,23 +939,38 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
             tr = I.vtrot[v];
             zb = cmul(za, tr);
             if (boundary) phi = fminf(fmaxf(phi, 0.f), T);
+            // the unit incoming direction and its angular position on the sheet [0, T) of an
+            // interior vertex (positions phi and phi + T are one direction; their unit numbers
+            // differ by the turn e^(i T), which is not 1 at a saddle)
             const double en_s = rsqrt(fma(E.x, E.x, E.y * E.y));
-            const double2 en = make_double2(E.x * en_s, E.y * en_s);   // unit incoming direction
+            double2 en = make_double2(E.x * en_s, E.y * en_s);
+            float phic = phi;
+            if (!boundary) {
+                const int kc = (int)floorf(phi / T);
+                phic = phi - (float)kc * T;
+                for (int q = 0; q < abs(kc) && q < 3; ++q) en = kc > 0 ? cmul_conj(en, tr) : cmul(en, tr);
+            }
             if (kind == 2) {
                 // a tie: fan only if its incoming direction differs from the last fan's
                 const float fp = I.fan_phi[v];
-                float dphi = fabsf(phi - fp);
+                float dphi = fabsf(phic - fp);
                 if (!boundary) {
                     dphi = fmodf(dphi, T);
                     dphi = fminf(dphi, T - dphi);
                 }
                 if (dphi < kTieSheet) {                // (a NaN, no fan recorded yet, fans)
+                    // the same direction up to FP32: compare the FP64 directions on one
+                    // sheet (the unit numbers of angular positions phi and phi + T differ
+                    // by the turn e^(i T), which is not 1 at a saddle or boundary vertex)
                     const double2 fd = I.fan_dir[v];
-                    if (fma(en.x, fd.x, en.y * fd.y) > 0.0 && fabs(fma(en.x, fd.y, -en.y * fd.x)) <= kTieDir) continue;
+                    const int sh = boundary ? 0 : (int)rintf((phic - fp) / T);
+                    double2 ea = en;
+                    for (int q = 0; q < abs(sh) && q < 3; ++q) ea = sh > 0 ? cmul_conj(ea, tr) : cmul(ea, tr);
+                    if (fma(ea.x, fd.x, ea.y * fd.y) > 0.0 && fabs(fma(ea.x, fd.y, -ea.y * fd.x)) <= kTieDir) continue;
                 }
                 if (sl == 0) atomicAdd(&cnt->fan_ties, 1ull);
             } else if (sl == 0) {
-                I.fan_phi[v] = phi;
+                I.fan_phi[v] = phic;
                 I.fan_dir[v] = en;
             }
             if (boundary) {
