@@ -926,7 +926,9 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
         // shifts of the total angle T): interior [phi + pi, phi + T - pi]; boundary
         // [-inf, phi - pi] and [phi + pi, +inf]
         const float T = I.vtheta[v];
-        double2 za = make_double2(0.0, 0.0), zb = za, tr = make_double2(1.0, 0.0), zlo = za, zhi = za;
+        double2 za = make_double2(0.0, 0.0), zb = za, tr = make_double2(1.0, 0.0), zlo = za, zhi = za, tie_z = za;
+        bool tie_lo = false, tie_hi = false;       // a tie's wedge cut to the part outside the last fan's
+        float tie_w = 0.f;
         int nw = 0;
         float wlo[2] = {0.f, 0.f}, whi[2] = {0.f, 0.f};
         bool lo_open[2] = {false, false}, hi_open[2] = {false, false};
@@ -945,8 +947,9 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
             const double en_s = rsqrt(fma(E.x, E.x, E.y * E.y));
             double2 en = make_double2(E.x * en_s, E.y * en_s);
             float phic = phi;
+            int kc = 0;
             if (!boundary) {
-                const int kc = (int)floorf(phi / T);
+                kc = (int)floorf(phi / T);
                 phic = phi - (float)kc * T;
                 for (int q = 0; q < abs(kc) && q < 3; ++q) en = kc > 0 ? cmul_conj(en, tr) : cmul(en, tr);
             }
@@ -969,6 +972,29 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
                     if (fma(ea.x, fd.x, ea.y * fd.y) > 0.0 && fabs(fma(ea.x, fd.y, -ea.y * fd.x)) <= kTieDir) continue;
                 }
                 if (sl == 0) atomicAdd(&cnt->fan_ties, 1ull);
+                // at an interior saddle whose two fanned areas overlap, only the part of this
+                // candidate's area outside the last fan's is new: the wedge between the two
+                // areas' upper (or lower) boundaries
+                if (!boundary && fp == fp) {
+                    const int sh = (int)rintf((phic - fp) / T);
+                    const float delta = phic - (fp + (float)sh * T);
+                    if (fabsf(delta) < T - 2.f * kPiF) {
+                        const int s2 = sh + kc;                  // the last fan's direction in this frame
+                        double2 fr = I.fan_dir[v];
+                        for (int q = 0; q < abs(s2) && q < 3; ++q) fr = s2 > 0 ? cmul(fr, tr) : cmul_conj(fr, tr);
+                        const float fraw = fp + (float)s2 * T;
+                        if (delta > 0.f) {
+                            tie_lo = true;
+                            tie_w = fraw + T - kPiF;
+                            const double2 t = cmul(fr, tr);
+                            tie_z = make_double2(-t.x, -t.y);
+                        } else {
+                            tie_hi = true;
+                            tie_w = fraw + kPiF;
+                            tie_z = make_double2(-fr.x, -fr.y);
+                        }
+                    }
+                }
             } else if (sl == 0) {
                 I.fan_phi[v] = phic;
                 I.fan_dir[v] = en;
@@ -986,6 +1012,8 @@ __global__ void __launch_bounds__(256) k_fan(Work w, int full_fan) {
             if (nw == 0) continue;
             zlo = za;
             zhi = boundary ? za : zb;
+            if (tie_lo) { wlo[0] = tie_w; zlo = tie_z; }
+            if (tie_hi) { whi[0] = tie_w; zhi = tie_z; }
         }
         bool deferred = false;
         for (int j0 = s; j0 < e && !deferred; j0 += kFanLanes) {
