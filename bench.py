@@ -612,9 +612,11 @@ NCU_CASES = {
                    {"k": 393216, "hops": 32, "block": 64}),
     "terrain512": (lambda mg: mg.workload("terrain", "full")[0][0], lambda mg, m: [mg.terrain_center(512, 512)],
                    {"k": 393216, "hops": 32, "block": 64}),
+    # the bench step's configuration (8 sources batched, learned control, 64 hops) on the
+    # same family at 2 subdivisions fewer (327,680 faces, about 2 GB on the device)
     "sphere7x8": (lambda mg: mg.multi_octave_sphere(7, 0.05, seed=mg.SEED_BASE + 5),
                   lambda mg, m: [int(x) for x in mg.pick_sources(m, 8, mg.SEED_BASE + 105)],
-                  {"k": 1 << 20, "hops": 64, "block": 64}),
+                  {"control": 1, "hops": 64, "block": 64}),
 }
 
 
@@ -626,6 +628,7 @@ def run_ncu_case(args):
     import __graft_entry__
     __graft_entry__.build()
     from paper_1305_1293_gb300 import meshgen as mg, pch
+    pch.load_controller()
     make, srcs, opts = NCU_CASES[args.ncu_case]
     m = make(mg)
     sv = srcs(mg, m)
@@ -636,6 +639,7 @@ def run_ncu_case(args):
         _, st = pch.solve_batch([h] * len(sv), sv, stats=True, loop=pch.LOOP_HOST, **opts)
     print(json.dumps({"ncu_case": args.ncu_case, "faces": m.nf, "sources": len(sv), "opts": opts,
                       "iterations": st["iterations"], "windows_propagated": st["windows_propagated"],
+                      "windows_examined": st["windows_examined"],
                       "kernel_launches": st["kernel_launches"], "prop_fp64_ops": st["prop_fp64_ops"]}), flush=True)
     h.close()
 
