@@ -48,6 +48,14 @@ FP64_PEAK_DERIVED = 152 * 4 * 2.07e9 / 1e12   # SMs x FP64 flops/clk/SM x max cl
 TUNE_CACHE = os.path.join(ROOT, "paper_1305_1293_gb300", "autotune_cache.txt")
 
 
+_T0 = time.time()
+
+
+def _log(msg):
+    """Progress of the run on stderr (the JSON line goes to stdout)."""
+    print(f"[bench {time.time() - _T0:7.1f} s] {msg}", file=sys.stderr, flush=True)
+
+
 def _peaks():
     """HBM copy bandwidth measured on this machine (MEASURED_PEAKS.json), else the fallback."""
     try:
@@ -275,7 +283,9 @@ def run_gpu(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # > L2 (129 MB)
     # the learned controller picks k each iteration; the tuner picks hops and the block
     t0 = time.perf_counter()
+    _log("mesh built; tuning hops and block for the learned control")
     tl = pch.autotune(h, sv[0], cache_path=TUNE_CACHE, control=pch.CONTROL_LEARNED)
+    _log(f"tuned {tl}")
     tune_learned_s = time.perf_counter() - t0
     lopts = {"control": pch.CONTROL_LEARNED, "hops": tl["hops"], "block": tl["block"]}
 
@@ -286,6 +296,7 @@ def run_gpu(args):
     for i in range(args.warmup):
         step(i)
     torch.cuda.synchronize()
+    _log("warm-up done")
     if ws > 1:
         torch.distributed.barrier()
     per_step, stats = [], []
@@ -316,7 +327,9 @@ def run_gpu(args):
         g0 = groups[0]
         # ---- plain PCH on the same GPU and group
         t0 = time.perf_counter()
+        _log("timed steps done; tuning the plain control")
         tp = pch.autotune(h, sv[0], cache_path=TUNE_CACHE)
+        _log(f"tuned {tp}")
         tune_plain_s = time.perf_counter() - t0
         popts = {"k": tp["k"], "hops": tp["hops"], "block": tp["block"]}
         seq_ms, seq_w = 0.0, 0
@@ -330,11 +343,13 @@ def run_gpu(args):
         t, (_, lst) = _timed(stream, lambda: pch.solve_batch([h] * len(g0), g0, outs=outs[:len(g0)], stats=True,
                                                              stream=stream, **lopts))
         lrn_g0_ms, lrn_g0_w = t, lst["windows_propagated"]
+        _log("plain arms done; the paper's setting")
         # the paper's setting: measured on the group's first source, counted for the group
         pch.solve(h, g0[0], out=outs[0], stream=stream, k=24576, hops=1)   # warm its graph
         t, (_, pst0) = _timed(stream, lambda: pch.solve(h, g0[0], out=outs[0], stats=True, stream=stream,
                                                          k=24576, hops=1))
         paper_ms_per_source = t
+        _log("profiled step")
         # ---- per-phase device time of one headline step (events around every phase)
         _, prof = pch.solve_batch([h] * len(g0), g0, stats=True, flags=pch.FLAG_PROFILE, **lopts)
         ph = prof["ms_phase"]
@@ -358,6 +373,7 @@ def run_gpu(args):
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
             e2e_w += st["windows_propagated"]
         e2e_value = e2e_w / (sum(e2e_ms) / 1e3)
+        _log("end to end done; parity samples")
         # ---- parity of the benchmarked fields on sampled vertices (oracle early stop)
         import oracle
         oracle.build()
@@ -367,7 +383,9 @@ def run_gpu(args):
             ref, _ = oracle.geodesic(m.vertices, m.faces, last_group[j], targets=near)
             parity = max(parity, float(np.max(np.abs(got[j][near] - ref[near]) / ref[near])))
         terrain = terrain_extras(pch, mg, stream)
+        _log("terrain done; CPU baseline")
         cpu = cpu_baseline_parallel(sv)
+        _log("CPU baseline done; full-field comparison")
         ff = full_field_comparison(pch, mg)
         clocks = clk.summary()
         ms_step = total_ms / args.steps

@@ -301,10 +301,11 @@ pch_status pch_trace_fetch(pch_mesh* m, int32_t max_rows, float* features, float
  * Times full solves of `src` on `m`: first the library defaults (k 24576, block 64, 32
  * hops), then a coordinate search over windows-per-iteration k (24576 times powers of 4,
  * up to 8x the face count, from the largest down until one is twice as slow as the best)
- * at block 128 and 16 hops, then hops (4, 8, 16, 32, 64), then propagation block sizes
- * (64, 128, 256); under PCH_CONTROL_LEARNED (the network picks k every iteration) only
- * hops and the block size are searched.  Each trial is timed on its second solve (the
- * first builds its graph).
+ * at block 128 and 16 hops, then hops (64, 32, 16, 8, 4, from the most down until one is
+ * twice as slow as the best), then propagation block sizes (64, 128, 256); under
+ * PCH_CONTROL_LEARNED (the network picks k every iteration) only hops and the block size
+ * are searched.  Each trial is timed on its second solve (the first builds its graph),
+ * unless its first solve was already twice as slow as the best.
  * Writes the fastest into opt->k, opt->block and opt->hops (the other fields of *opt are
  * kept and used for every trial) and its time into *best_ms (may be NULL).  If
  * cache_path is not NULL the result is looked up first in, and then appended to, that

@@ -2303,6 +2303,7 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
             pch_status rc = solve_instances(&m, 1, &sd, 1, &trial, nullptr, kOutNone, &st);
             if (rc != PCH_OK) return rc;
             ms = st.ms_total;
+            if (rep == 0 && ms > 2.0 * best) break;   // far from the best: no second timing
         }
         return PCH_OK;
     };
@@ -2329,8 +2330,15 @@ extern "C" pch_status pch_autotune(pch_mesh* m, const pch_source* src, pch_optio
         if (ms > 2.0 * best) break;
     }
     const long long k_sel = best_k;
-    for (int hp : hopss)
-        if ((learned || hp != 16) && (rc = consider(k_sel, 128, hp)) != PCH_OK) return rc;
+    // hops from the most down, stopping once a setting is twice as slow as the best
+    for (int q = 4; q >= 0; --q) {
+        const int hp = hopss[q];
+        if (!learned && hp == 16) continue;
+        double ms = 0.0;
+        if ((rc = time_cfg(k_sel, 128, hp, ms)) != PCH_OK) return rc;
+        if (ms < best) { best = ms; best_k = k_sel; best_b = 128; best_h = hp; }
+        if (ms > 2.0 * best) break;
+    }
     const int h_sel = best_h;
     for (int b : blocks)
         if (b != 128 && (rc = consider(k_sel, b, h_sel)) != PCH_OK) return rc;
