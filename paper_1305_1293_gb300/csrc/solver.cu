@@ -1755,8 +1755,11 @@ pch_status solve_instances(pch_mesh* const* meshes, int n_inst, const SrcDev* sr
         c.active = 1;
     }
     // the work list never needs more than the pending windows, which rarely exceed the
-    // half-edge count; a larger k only leaves the rest pending
-    long long sel_want = std::max<long long>(65536, 4LL * cfg.k * std::min(n_inst, 64));
+    // half-edge count; a larger k only leaves the rest pending.  Under the learned control
+    // the network may pick up to 2^26 windows an iteration: the list is sized for that
+    // (within the same caps), not for the plain k it falls back to
+    const long long k_size = cfg.control == PCH_CONTROL_LEARNED ? std::max<long long>(cfg.k, 1LL << 22) : cfg.k;
+    long long sel_want = std::max<long long>(65536, 4LL * k_size * std::min(n_inst, 64));
     sel_want = std::min<long long>(sel_want, std::max<long long>(65536, aoff));
     sel_want = std::min<long long>(sel_want, 1 << 24);
     int pool_want = (int)std::min<long long>(std::max<long long>(2 * 6 * sel_want, 1 << 20), (1LL << 30));
