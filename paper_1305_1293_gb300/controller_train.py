@@ -26,7 +26,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 WEIGHTS = os.path.join(HERE, "controller_weights.npy")
 TRAIN_SEED = 0x7A1E5
-SWEEP_K = (4096, 16384, 65536, 262144, 1048576, 4194304)
+SWEEP_K = (4096, 16384, 65536, 262144, 1048576, 4194304, 16777216)
 
 
 def training_set():
