@@ -844,7 +844,11 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
 // corner's end, so the choice never changes a window.
 constexpr float kPiF = 3.14159265358979f;
 constexpr float kFanPickMargin = 1e-4f;   // radians: corners within this of a wedge boundary are computed exactly
-constexpr double kFanWiden = 1e-9;        // interval widening for FP64 rounding, relative to the edge length
+// interval widening for FP64 rounding, relative to the edge length: the fanned area's
+// boundary and the children of windows passing the vertex are computed from different
+// unfoldings, whose pseudo-source coordinates carry rounding accumulated over long
+// lineages (up to about 1e-10 of the edge on the 5.2M-face sphere)
+constexpr double kFanWiden = 1e-7;
 constexpr int kFanLanes = 8;              // lanes per fan candidate (corners handled in turn)
 // Ties: a fan candidate whose distance equals the vertex's final one within the filters'
 // margin but that did not make the iteration's fan (another candidate did) is deferred to
