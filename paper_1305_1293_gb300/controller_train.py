@@ -2,7 +2,7 @@
 
 Recipe (build-side; the paper fixes k by hand, Section 5.2):
   1. Training meshes: icospheres, geodesic spheres, terrains, jittered tori and
-     multi-octave spheres of 5K-330K faces, seeds disjoint from every benchmark
+     multi-octave spheres of 5K-1.3M faces, seeds disjoint from every benchmark
      workload (``TRAIN_SEED``), one or two random sources each.
   2. Threshold sweep: solve each with the plain control at k in ``SWEEP_K`` and record
      every iteration's frontier features (PCH_FLAG_TRACE) and the solve time.
@@ -42,12 +42,18 @@ def training_set():
             mg.multi_octave_sphere(7, 0.05, seed=s + 3), mg.geodesic_sphere(120, 0.02, seed=s + 4),
             mg.torus(900, 250, seed=s + 5), mg.geodesic_sphere(90, 0.05, seed=s + 6),
             mg.torus(400, 130, jitter=0.2, seed=s + 7)]
+    # large meshes (0.8M-1.3M faces): where a small k multiplies the iterations
+    s = TRAIN_SEED + 20
+    out += [mg.multi_octave_sphere(8, 0.05, seed=s), mg.geodesic_sphere(200, 0.02, seed=s + 1),
+            mg.terrain(640, 640, seed=s + 2), mg.torus(1100, 380, seed=s + 3)]
     return out
 
 
 def sweep(pch, mesh_np, sources, ks=SWEEP_K):
     """Features, labels and per-k solve times of one training mesh."""
-    if mesh_np.nf > 100000:
+    if mesh_np.nf > 500000:
+        ks = tuple(k for k in ks if k >= 262144)     # smaller k are far from best there, and slow
+    elif mesh_np.nf > 100000:
         ks = tuple(k for k in ks if k >= 16384)      # k = 4096 is far from best there, and slow
     mesh = pch.Mesh(mesh_np.vertices, mesh_np.faces)
     feats, labels, times = [], [], {}
