@@ -146,7 +146,7 @@ __global__ void k_frames(int nh, const double* __restrict__ xyz, const int* __re
         double yc = sqrt(t > 0.0 ? t : 0.0);
         HERec r;
         r.L = L; r.xc = xc; r.yc = yc; r.L1 = L1; r.L2 = L2;
-        r.iL1 = 1.0 / L1; r.iL2 = 1.0 / L2; r.iLq = (double)(1 << kAngleXBits) / L; r.pad = 0.0;
+        r.u1x = (L - xc) / L1; r.u1y = -yc / L1; r.u2x = xc / L2; r.u2y = yc / L2;
         r.tw1 = r.tw2 = r.twin = -1;
         r.v0 = a; r.v1 = b; r.v2 = c;
         rec[h] = r;

@@ -40,9 +40,8 @@ constexpr int kHidden = 64;
 struct __align__(16) HERec {
     double L, xc, yc;      // edge length and apex position
     double L1, L2;         // |v1 v2|, |v2 v0|
-    double iL1, iL2;       // reciprocals of L1, L2
-    double iLq;            // 2^kAngleXBits / L: crossing position -> angle_split units
-    double pad;
+    double u1x, u1y;       // unit vector from v2 to v1: the right child's edge axis
+    double u2x, u2y;       // unit vector from v0 to v2: the left child's edge axis
     int tw1;               // twin of next(h) = (v2 -> v1) in the neighbour: right child's edge
     int tw2;               // twin of prev(h) = (v0 -> v2) in the neighbour: left child's edge
     unsigned v0, v1, v2;   // vertex ids | kPseudoBit

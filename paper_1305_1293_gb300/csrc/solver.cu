@@ -580,7 +580,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                 const double xcl = lt_s(xs, A) ? A : (lt_s(B, xs) ? B : xs);
                 // angle_split position: xs in units of 2^-24 |e| (only the order of positions
                 // on one edge matters, so any fixed scale per edge will do)
-                const double xq = xs * R.iLq;
+                const double xq = xs * (rcp_nr(L) * (double)(1 << kAngleXBits));
                 const double dx = xc - px, dy = yc - py;
                 Iv2 = sqrt_nr(dx * dx + dy * dy);
                 const double D2 = d + Iv2;
@@ -605,7 +605,7 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                     // the ray arrives at v2 inside face(h); direction to I in the frame of
                     // prev(h) = (v2 -> v0), whose axis is (-xc, -yc) / L2
                     const int hp = 3 * (h / 3) + (h % 3 + 2) % 3;
-                    const double ux = -xc * R.iL2, uy = -yc * R.iL2, ex = px - xc, ey = py - yc;
+                    const double ux = -R.u2x, uy = -R.u2y, ex = px - xc, ey = py - yc;
                     push_fan(req, &cnt->n_req, w.req_cap, &cnt->error, inst, R.v2 & ~kPseudoBit, D2, hp,
                              ex * ux + ey * uy, ux * ey - uy * ex, ev);
                 }
@@ -645,9 +645,8 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                 // both sides as one select-driven path (a warp holds left and right children)
                 const double Lc = rt ? R.L1 : R.L2;
                 const double ox = rt ? xc : 0.0, oy = rt ? yc : 0.0;
-                const double sc = rt ? R.iL1 : R.iL2;
-                const double ux = (rt ? L - xc : xc) * sc;
-                const double uy = (rt ? -yc : yc) * sc;
+                const double ux = rt ? R.u1x : R.u2x;
+                const double uy = rt ? R.u1y : R.u2y;
                 const double rx = px - ox, ry = py - oy;
                 const double Ipx = fma(rx, ux, ry * uy), Ipy = fma(ux, ry, -(uy * rx));
                 const double upy = ux * py, rpy = rx * py;
@@ -871,7 +870,7 @@ __device__ __forceinline__ double2 cmul_conj(double2 a, double2 b) {   // a * co
 // Where the ray from the apex v of o's face along z (relative to the direction
 // v -> start(o), any length) meets o: distance from start(o), clamped to [0, L].
 __device__ __forceinline__ double fan_hit(const HERec& Ro, double2 z) {
-    const double ux = -Ro.xc * Ro.iL2, uy = -Ro.yc * Ro.iL2;   // v -> start(o), unit
+    const double ux = -Ro.u2x, uy = -Ro.u2y;                   // v -> start(o), unit
     const double dx = fma(ux, z.x, -uy * z.y), dy = fma(ux, z.y, uy * z.x);
     if (!(dy < 0.0)) return dx > 0.0 ? Ro.L : 0.0;             // parallel to o or turned away
     const double s = fma(-Ro.yc * dx, rcp_nr(dy), Ro.xc);
@@ -1617,12 +1616,13 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         // counted per code path of propagate_window: a window taken from the work list 7
         // (2 offsets, 5 for the endpoint filter), a chained window 2 (its filter was its
         // parent's child filter), a window that passed +9 (occupancy test), an occupied
-        // one +15 (crossing point and its angle_split position, |I v2|, event distance),
-        // a child +28 (frame change 10, width 1, child filter 16, key 1) plus 8 per ray
-        // intersected (two per child, one when the window occupies v2)
+        // one +17 (crossing point and its angle_split position, |I v2|, event distance),
+        // a child +25 (frame change 7: the child edge's unit axis comes with the half-edge
+        // record; width 1, child filter 16, key 1) plus 8 per ray intersected (two per
+        // child, one when the window occupies v2)
         const unsigned long long fresh = c.examined > c.chained ? c.examined - c.chained : 0ull;
         stats->prop_fp64_ops = (int64_t)(7ull * fresh + 2ull * c.chained + 9ull * c.propagated +
-                                         15ull * c.occupied + 28ull * c.children + 8ull * c.rays);
+                                         17ull * c.occupied + 25ull * c.children + 8ull * c.rays);
         for (int p = 0; p < 6; ++p) stats->ms_phase[p] = phase_ms[p];
     }
     return PCH_OK;
