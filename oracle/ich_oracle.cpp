@@ -265,18 +265,19 @@ struct Solver {
 
     // Xin-Wang filter (Fig. `fig:filter`(b)) on a new window lying on half-edge c
     // (start cs, end ce) inside face (v0,v1,v2), with |IX| at its endpoints given.
-    // `third`, `third_at_b`, `d_third`: the vertex of the parent's edge that is not on
-    // the new edge, whether the test point is the endpoint nearer ce (B) or cs (A), and
-    // the in-face distance from that vertex to the test point.
+    // `third`, `dA_third`, `dB_third`: the vertex of the parent's edge that is not on the
+    // new edge and its in-face distances to the window's ends A and B.  The paper prints
+    // the third inequality at one end; the window is useless against that vertex only if
+    // the path through it is shorter over the whole interval, and d + |I x| - |third x|
+    // has no interior minimum there (its one critical point on the line is a maximum), so
+    // the test is made at both ends.
     bool ich_useless(double d, double a, double b, double Lc, double IA, double IB, int cs, int ce,
-                     int third, bool third_at_b, double d_third) const {
+                     int third, double dA_third, double dB_third) const {
         if (flags & NO_ICH) return false;
         if (dominated(d + IB, g[cs] + b)) return true;            // vs the start vertex, at B
         if (dominated(d + IA, g[ce] + (Lc - a))) return true;     // vs the end vertex, at A
-        if (third >= 0) {
-            double lhs = d + (third_at_b ? IB : IA);
-            if (dominated(lhs, g[third] + d_third)) return true;  // vs the parent edge's far vertex
-        }
+        if (third >= 0 && dominated(d + IA, g[third] + dA_third) && dominated(d + IB, g[third] + dB_third))
+            return true;                                          // vs the parent edge's far vertex
         return false;
     }
 
@@ -298,7 +299,7 @@ struct Solver {
             w.src = v;
             // ICH filter on the new window: vs b at B (the a end), vs a at A (the b end);
             // the third vertex is v itself, i.e. the test reads D > g[v].
-            if (ich_useless(D, 0.0, m.len[t], m.len[t], vb, va, b, a, v, true, va)) continue;
+            if (ich_useless(D, 0.0, m.len[t], m.len[t], vb, va, b, a, v, vb, va)) continue;
             push(w);
         }
     }
@@ -401,9 +402,9 @@ struct Solver {
                     if (tb - ta > kEpsTiny * Lc) {
                         double IA = std::hypot(ta * ux - px, ta * uy - py);
                         double IB = std::hypot(tb * ux - px, tb * uy - py);
-                        // third vertex: v1 (parent edge {v0,v1}, shared vertex v0 -> test at A)
-                        double v1A = std::hypot(ta * ux - L, ta * uy);
-                        if (!ich_useless(w.d, ta, tb, Lc, IA, IB, v0, v2, v1, false, v1A))
+                        // third vertex: v1 (parent edge {v0,v1})
+                        double v1A = std::hypot(ta * ux - L, ta * uy), v1B = std::hypot(tb * ux - L, tb * uy);
+                        if (!ich_useless(w.d, ta, tb, Lc, IA, IB, v0, v2, v1, v1A, v1B))
                             push(child(Window{w.d, ta, tb, w.d0, Iv2, c}, w));
                     }
                 }
@@ -427,9 +428,9 @@ struct Solver {
                         double bx = xc + tb * ux, by = yc + tb * uy;
                         double IA = std::hypot(ax - px, ay - py);
                         double IB = std::hypot(bx - px, by - py);
-                        // third vertex: v0 (shared vertex v1 -> test at B)
-                        double v0B = std::hypot(bx, by);
-                        if (!ich_useless(w.d, ta, tb, Lc, IA, IB, v2, v1, v0, true, v0B))
+                        // third vertex: v0 (parent edge {v0,v1})
+                        double v0A = std::hypot(ax, ay), v0B = std::hypot(bx, by);
+                        if (!ich_useless(w.d, ta, tb, Lc, IA, IB, v2, v1, v0, v0A, v0B))
                             push(child(Window{w.d, ta, tb, Iv2, w.d1, c}, w));
                     }
                 }

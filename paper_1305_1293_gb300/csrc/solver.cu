@@ -668,14 +668,19 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                 if (!lt_s(times_eps(Lc), b - a)) continue;
                 // Xin-Wang filter (Fig. `fig:filter`(b)) on the new window: against its
                 // start and end vertices (right child: v2, v1; left child: v0, v2), and
-                // against the vertex of the parent edge off the child's edge, tested at the
-                // child's endpoint nearer the shared vertex (right: v0 at b; left: v1 at a).
+                // against the vertex T of the parent edge off the child's edge (right: v0;
+                // left: v1), at both ends of the child: d + |I x| - |T x| has no interior
+                // minimum on the child's interval (its only critical point on the line is a
+                // maximum, where the line from I through T crosses it), so the path via T
+                // beats the whole window exactly when it beats both ends.
                 const double gS = rt ? g2 : g0, gE = rt ? g1 : g2, gT = rt ? g0 : g1;
                 const double dA = d + IAc, dB = d + IBc;
-                const double tT = rt ? b : a;
-                const double Xx = fma(tT, ux, rt ? xc : -L), Xy = fma(tT, uy, oy);
+                const double Tx = rt ? xc : -L;           // the child's origin relative to T
+                const double Xax = fma(a, ux, Tx), Xay = fma(a, uy, oy);
+                const double Xbx = fma(b, ux, Tx), Xby = fma(b, uy, oy);
                 const bool useless = dominated(dB, gS + b) || dominated(dA, gE + (Lc - a)) ||
-                                     dominated_sq(rt ? dB : dA, gT, fma(Xx, Xx, Xy * Xy));
+                                     (dominated_sq(dA, gT, fma(Xax, Xax, Xay * Xay)) &&
+                                      dominated_sq(dB, gT, fma(Xbx, Xbx, Xby * Xby)));
                 if (useless) continue;
                 const ChildOut co{rt ? R.tw1 : R.tw2, a, b, Ipx, Ipy, child_key(d, a, b, Ipx, Ipy, IAc, IBc), IAc, IBc};
                 if (nch == 0) c0 = co;
@@ -1619,7 +1624,9 @@ static pch_status run_solve(Workspace* ws, cudaStream_t s, const SolveCfg& cfg_i
         // one +17 (crossing point and its angle_split position, |I v2|, event distance),
         // a child +25 (frame change 7: the child edge's unit axis comes with the half-edge
         // record; width 1, child filter 16, key 1) plus 8 per ray intersected (two per
-        // child, one when the window occupies v2)
+        // child, one when the window occupies v2); the filter's test against the parent
+        // edge's far vertex at the second end (+11) is not counted: it is evaluated only
+        // where the first end's test holds (the warp runs it when any lane needs it)
         const unsigned long long fresh = c.examined > c.chained ? c.examined - c.chained : 0ull;
         stats->prop_fp64_ops = (int64_t)(7ull * fresh + 2ull * c.chained + 9ull * c.propagated +
                                          17ull * c.occupied + 25ull * c.children + 8ull * c.rays);

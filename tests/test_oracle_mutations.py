@@ -23,7 +23,8 @@ MUTATIONS = {
     "loser_keeps_wrong_child": (
         "if (xs < aX[h] - tol) left = true;\n                else if (xs > aX[h] + tol) right = true;",
         "if (xs < aX[h] - tol) right = true;\n                else if (xs > aX[h] + tol) left = true;"),
-    "third_test_wrong_end": ("v0, v2, v1, false, v1A", "v0, v2, v1, true, v1A"),
+    "third_test_either_end": ("dominated(d + IA, g[third] + dA_third) && dominated",
+                              "dominated(d + IA, g[third] + dA_third) || dominated"),
     "no_pseudo_sources": ("m.pseudo[v] = boundary[v] || theta[v] > kTwoPi - 1e-9;", "m.pseudo[v] = 0;"),
     "no_boundary_pseudo_sources": ("m.pseudo[v] = boundary[v] || theta[v] > kTwoPi - 1e-9;",
                                    "m.pseudo[v] = theta[v] > kTwoPi - 1e-9;"),
