@@ -628,8 +628,9 @@ NCU_CASES = {
     # k-th iteration's
     "terrain256": (lambda mg: mg.terrain(256, 256, seed=mg.SEED_BASE + 1), lambda mg, m: [mg.terrain_center(256, 256)],
                    {"k": 393216, "hops": 32, "block": 64}),
+    # the terrain's autotuned configuration on a GB300
     "terrain512": (lambda mg: mg.workload("terrain", "full")[0][0], lambda mg, m: [mg.terrain_center(512, 512)],
-                   {"k": 393216, "hops": 32, "block": 64}),
+                   {"k": 1572864, "hops": 32, "block": 64}),
     # the bench step's configuration (8 sources batched, learned control, 64 hops) on the
     # same family at 2 subdivisions fewer (327,680 faces, about 2 GB on the device)
     "sphere7x8": (lambda mg: mg.multi_octave_sphere(7, 0.05, seed=mg.SEED_BASE + 5),
