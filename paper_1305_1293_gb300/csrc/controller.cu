@@ -51,6 +51,15 @@ int default_hops() {
     return 32;
 }
 
+int default_take_min() {
+    const char* e = std::getenv("PCH_TAKE_MIN");
+    if (e) {
+        int v = std::atoi(e);
+        if (v >= 1 && v <= 32) return v;
+    }
+    return 1;
+}
+
 int default_tail_cut() {
     const char* e = std::getenv("PCH_TAIL_CUT");
     if (e) {

@@ -706,10 +706,13 @@ constexpr int kPropMaxWarps = 8;      // warps per block at most (256 threads)
 // full).  Repacking the chains onto the warp's lowest lanes every round keeps the lanes
 // that issue FP64 work together; no warp waits for another (only __syncwarp between
 // rounds), and a warp leaves once the selected list is exhausted and its queue is empty.
+// A warp takes at most ceil(selected / resident warps) fresh windows at once (take_min
+// at least), so that a short list (the first iterations, a ring-shaped frontier) keeps
+// every resident warp busy and the chains' deferred children fill the free lanes.
 // 168 registers a thread at most (152 used, no spills): 6 blocks of 64 threads per SM.
 // PROV: also record the distance events (geodesic paths).
 template <bool PROV>
-__global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
+__global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut, int take_min) {
     extern __shared__ double q_mem[];   // blockDim.x * kPropQueueBytesPerThread bytes
     const int QB = 2 * blockDim.x;
     double* q_d = q_mem;
@@ -735,6 +738,13 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
     const int n = min(cnt->n_sel, w.sel_cap);
     FanReq* req = w.req[it & 1];
     const int room = w.arena_cap / 2 - 2 * (int)(gridDim.x * blockDim.x);
+    // Fresh windows a warp holds at once: a short selected list is spread over all
+    // resident warps (take_min a warp at least), so that the lanes left free take the
+    // deferred children of the chains instead of the arena; a list of a warp's width per
+    // resident warp or more fills whole warps.
+    const int nwarps = (int)(gridDim.x * (blockDim.x >> 5));
+    const int quota = max(take_min, min(32, (n + nwarps - 1) / max(nwarps, 1)));
+    const unsigned take_mask = quota >= 32 ? 0xffffffffu : (1u << quota) - 1u;
     // the arena fill this warp last saw (updated whenever it reserves arena slots): a
     // warp overshoots the room by at most one round of its own writes
     int seen_child = *(volatile int*)&cnt->n_child;
@@ -760,13 +770,13 @@ __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut) {
             d = q_d[qr]; A = q_A[qr]; B = q_B[qr]; px = q_px[qr]; py = q_py[qr];
             cIA = q_IA[qr]; cIB = q_IB[qr];
         }
-        const unsigned need = __ballot_sync(full, !have);
+        const unsigned need = __ballot_sync(full, !have) & take_mask;   // lanes nq.. below the quota
         if (need && !dry) {
             int base = 0;
             if (lane == 0) base = atomicAdd(&cnt->work_next, __popc(need));
             base = __shfl_sync(full, base, 0);
             if (base + __popc(need) >= n) dry = true;
-            if (!have) {
+            if ((need >> lane) & 1u) {
                 const int idx = base + __popc(need & lt);
                 if (idx < n) {
                     h = w.sel.he[idx]; inst = w.sel.inst[idx]; d = w.sel.d[idx]; src = w.sel.src[idx];
@@ -1467,8 +1477,8 @@ static cudaError_t launch_iteration(Workspace* ws, cudaStream_t s, const SolveCf
     if (ev) cudaEventRecord(ev[1], s);
     const dim3 pg(grid_for(cfg.prop_blocks_per_sm));
     const size_t psh = (size_t)cfg.prop_threads * kPropQueueBytesPerThread;
-    if (cfg.prov) k_propagate<true><<<pg, cfg.prop_threads, psh, s>>>(w, cfg.hops, cfg.tail_cut);
-    else k_propagate<false><<<pg, cfg.prop_threads, psh, s>>>(w, cfg.hops, cfg.tail_cut);
+    if (cfg.prov) k_propagate<true><<<pg, cfg.prop_threads, psh, s>>>(w, cfg.hops, cfg.tail_cut, cfg.take_min);
+    else k_propagate<false><<<pg, cfg.prop_threads, psh, s>>>(w, cfg.hops, cfg.tail_cut, cfg.take_min);
     if (ev) cudaEventRecord(ev[2], s);
     if (cfg.prov) k_fan<true><<<grid_for(2), 256, 0, s>>>(w, cfg.full_fan);
     else k_fan<false><<<grid_for(2), 256, 0, s>>>(w, cfg.full_fan);
@@ -1648,6 +1658,7 @@ static SolveCfg make_cfg(const pch_options* opt, int n_inst, long long total_key
     cfg.profile = (opt && (opt->flags & PCH_FLAG_PROFILE)) ? 1 : 0;
     cfg.hops = (opt && opt->hops > 0) ? opt->hops : default_hops();
     cfg.tail_cut = default_tail_cut();
+    cfg.take_min = default_take_min();
     cfg.unroll = 2;
     // Step 3 organises the new windows into a gap-free pool; they are grouped by instance
     // (one 8-bit radix pass for up to 256 instances, none for one), or with

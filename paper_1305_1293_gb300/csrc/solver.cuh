@@ -26,6 +26,7 @@ struct SolveCfg {
     int profile;
     int hops;
     int tail_cut;           // stop chaining once the selected list is dry and fewer entries are queued
+    int take_min;           // fresh windows a propagation warp may take at once, at least (32: a full warp)
     int stride_T;           // PCH_CONTROL_STRIDED: virtual threads of the strided selection (else 0)
     int stride_m;           // PCH_CONTROL_STRIDED: windows each of them selects (1, 2, 4, 8 or 16)
     int prov;               // record distance events for geodesic paths
@@ -38,6 +39,7 @@ long long default_k();
 int default_hops();
 int default_prop_blocks_per_sm(int block);
 int default_tail_cut();
+int default_take_min();
 const float* mlp_device_params();
 
 // prov: also record every distance event that lowered a vertex's distance (geodesic
