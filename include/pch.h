@@ -58,8 +58,9 @@ typedef struct {
 /* Selection control (Step 1 of Section 4.2). */
 enum {
     PCH_CONTROL_PLAIN = 0,    /* fixed window count k per iteration (the paper's k) */
-    PCH_CONTROL_LEARNED = 1,  /* MLP controller maps frontier statistics to the threshold;
-                                 falls back to PLAIN on a non-finite or out-of-range output,
+    PCH_CONTROL_LEARNED = 1,  /* MLP controller maps frontier statistics to log2 of the
+                                 number of windows to select, clamped to the trained range
+                                 [2^12, 2^24]; falls back to PLAIN on a non-finite output,
                                  and runs PLAIN when no weights were installed
                                  (pch_mlp_set_weights) on the current device since its
                                  CUDA context was created */

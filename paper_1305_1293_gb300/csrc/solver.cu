@@ -328,9 +328,11 @@ __global__ void k_tau(Work w, int control, const float* __restrict__ mlp) {
             long long k = c.k_target;
             if (learned) {
                 c.ctl_out = y;
-                // y = log2(windows to select) / 24; the plain k when the output is not
-                // finite or outside [2^8, 2^26]
-                if (isfinite(y) && y >= 8.f / 24.f && y <= 26.f / 24.f) k = (long long)exp2(24.0 * (double)y);
+                // y = log2(windows to select) / 24, clamped to the range of k the network
+                // was trained on (2^12 to 2^24); the plain k only when it is not finite.
+                // (Falling back to the plain k for a finite output beyond that range, a
+                // small k under this control, made late iterations select few windows.)
+                if (isfinite(y)) k = (long long)exp2(24.0 * (double)fminf(fmaxf(y, 12.f / 24.f), 1.f));
             }
             if (np == 0) {
                 tau = -INFINITY;

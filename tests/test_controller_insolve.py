@@ -135,8 +135,8 @@ def test_trace_row_properties(pch):
 
 
 def _random_controller(seed):
-    """Weights whose outputs stay mostly inside the controller's range [8/24, 26/24], so
-    that the network, not the plain fallback, decides most iterations."""
+    """Weights whose outputs stay mostly inside the controller's range [12/24, 1], so that
+    most iterations take the network's k unclamped."""
     from paper_1305_1293_gb300.meshgen import SplitMix64
     p = mo.init_params(seed) * 0.5
     q = mo.unpack(p)
@@ -154,12 +154,16 @@ def _check_learned_choices(feats, chosen, params, plain_k):
     delta = 24 * 1e-4                                 # FP32 network vs FP64: |dy| <= 1e-4
     for j in range(len(y)):
         a = 24.0 * y[j]
-        if 8 + delta <= a <= 26 - delta:
+        if not math.isfinite(a):
+            assert abs(lk[j] - math.log2(plain_k)) < 1e-5, (j, a, lk[j])
+        elif 12 + delta <= a <= 24 - delta:
             # k = floor(2^(24 y)) with y within delta of the FP64 value
             assert math.log2(2.0 ** (a - delta) - 1) - 1e-5 <= lk[j] <= a + delta + 1e-5, (j, a, lk[j])
             used_net += 1
-        elif a < 8 - delta or a > 26 + delta or not math.isfinite(a):
-            assert abs(lk[j] - math.log2(plain_k)) < 1e-5, (j, a, lk[j])
+        elif a < 12 - delta or a > 24 + delta:
+            # clamped to the trained range: exactly 2^12 or 2^24
+            assert abs(lk[j] - (12.0 if a < 12 else 24.0)) < 1e-5, (j, a, lk[j])
+            used_net += 1
     return used_net
 
 
