@@ -266,11 +266,12 @@ struct Solver {
     // Xin-Wang filter (Fig. `fig:filter`(b)) on a new window lying on half-edge c
     // (start cs, end ce) inside face (v0,v1,v2), with |IX| at its endpoints given.
     // `third`, `dA_third`, `dB_third`: the vertex of the parent's edge that is not on the
-    // new edge and its in-face distances to the window's ends A and B.  The paper prints
-    // the third inequality at one end; the window is useless against that vertex only if
-    // the path through it is shorter over the whole interval, and d + |I x| - |third x|
-    // has no interior minimum there (its one critical point on the line is a maximum), so
-    // the test is made at both ends.
+    // new edge and its in-face distances to the window's ends A and B.  The paper tests
+    // the third inequality at the end nearer the vertex that the new edge shares with the
+    // parent edge, where d + |I x| - |third x| takes its smallest value over the interval;
+    // here the window is dropped only when both ends are dominated: the same decision in
+    // exact arithmetic, and the safe one when rounding puts one end's test on the wrong
+    // side of the margin.
     bool ich_useless(double d, double a, double b, double Lc, double IA, double IB, int cs, int ce,
                      int third, double dA_third, double dB_third) const {
         if (flags & NO_ICH) return false;

@@ -671,10 +671,11 @@ __device__ __forceinline__ bool propagate_window(const Work& w, Counters* cnt, F
                 // Xin-Wang filter (Fig. `fig:filter`(b)) on the new window: against its
                 // start and end vertices (right child: v2, v1; left child: v0, v2), and
                 // against the vertex T of the parent edge off the child's edge (right: v0;
-                // left: v1), at both ends of the child: d + |I x| - |T x| has no interior
-                // minimum on the child's interval (its only critical point on the line is a
-                // maximum, where the line from I through T crosses it), so the path via T
-                // beats the whole window exactly when it beats both ends.
+                // left: v1), at both ends of the child.  d + |I x| - |T x| is smallest at
+                // the end nearer the vertex shared with the parent edge (the end the paper
+                // tests); requiring both ends is the same decision in exact arithmetic and
+                // keeps the child when rounding puts one end's test on the wrong side of
+                // the margin.
                 const double gS = rt ? g2 : g0, gE = rt ? g1 : g2, gT = rt ? g0 : g1;
                 const double dA = d + IAc, dB = d + IBc;
                 const double Tx = rt ? xc : -L;           // the child's origin relative to T
