@@ -712,7 +712,7 @@ constexpr int kPropMaxWarps = 8;      // warps per block at most (256 threads)
 // A warp takes at most ceil(selected / resident warps) fresh windows at once (take_min
 // at least), so that a short list (the first iterations, a ring-shaped frontier) keeps
 // every resident warp busy and the chains' deferred children fill the free lanes.
-// 168 registers a thread at most (152 used, no spills): 6 blocks of 64 threads per SM.
+// 168 registers a thread at most (164 used, no spills): 6 blocks of 64 threads per SM.
 // PROV: also record the distance events (geodesic paths).
 template <bool PROV>
 __global__ void __maxnreg__(168) k_propagate(Work w, int hops, int tail_cut, int take_min) {
