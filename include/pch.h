@@ -17,6 +17,17 @@
  *    pch_options.stream (or the legacy default stream) reaches the end of the call.
  *  - Calls that share a pch_mesh (it carries the solver workspace) must not run
  *    concurrently from several host threads.
+ *
+ * Environment variables (read each time a solve sets up its configuration; defaults in
+ * brackets; invalid values are ignored).  They change speed, never the distances:
+ *  - PCH_DEFAULT_K [24576]: windows selected per iteration when pch_options.k <= 0.
+ *  - PCH_DEFAULT_HOPS [32]: chained propagation hops when pch_options.hops <= 0.
+ *  - PCH_TAKE_MIN [1, range 1..32]: fresh windows a propagation warp takes at once, at
+ *    least (a short selected list is spread over every resident warp above this floor).
+ *  - PCH_TAIL_CUT [0]: once the selected list is exhausted, a warp keeps chaining only
+ *    while it holds at least this many queued windows.
+ *  - PCH_PROP_BLOCKS_PER_SM [384 / block threads, range 1..32]: resident propagation
+ *    blocks per SM (the grid is this times the SM count).
  */
 #ifndef PCH_H_
 #define PCH_H_
